@@ -1,0 +1,264 @@
+"""ctypes wrapper around the plain FP64 MOREA oracle (``morea_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  The product path
+(``paper_2303_04873_gb300``) never imports it, and it never imports the
+product.  ``build()`` compiles the C oracle with the host compiler into
+``oracle/_build/`` (plain C99 + libm, so it builds the same on x86-64 and
+aarch64).
+
+Parity status of each oracle function (what pins it) is listed in
+``tests/test_oracle_pins.py``; every function here is pinned there.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "libmorea_oracle.so")
+_SRC = os.path.join(_HERE, "morea_oracle.c")
+
+TET_DTYPE = np.dtype([
+    ("e_img", "<f8", (2,)), ("e_guid", "<f8", (2,)),
+    ("n_vox", "<i8", (2,)), ("n_gp", "<i8", (2,)),
+    ("e_mag", "<f8"), ("sev", "<u8"), ("folded", "<i4"), ("pad", "<i4"),
+])
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32), ("pad0", ctypes.c_int32),
+        ("img_s", ctypes.c_void_p), ("img_t", ctypes.c_void_p),
+        ("n_points", ctypes.c_int32), ("n_tets", ctypes.c_int32),
+        ("tets", ctypes.c_void_p), ("ref_points", ctypes.c_void_p),
+        ("tet_label", ctypes.c_void_p), ("tissue_factor", ctypes.c_void_p),
+        ("n_labels", ctypes.c_int32), ("n_guid", ctypes.c_int32),
+        ("guid_s", ctypes.c_void_p), ("guid_t", ctypes.c_void_p), ("guid_group", ctypes.c_void_p),
+        ("trunc_radius", ctypes.c_double),
+        ("h_mode", ctypes.c_int32), ("g_mode", ctypes.c_int32),
+        ("subvoxel_bits", ctypes.c_int32), ("pad1", ctypes.c_int32),
+    ]
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [
+        ("obj", ctypes.c_double * 3), ("severity", ctypes.c_double),
+        ("s_img", ctypes.c_double), ("s_guid", ctypes.c_double), ("s_mag", ctypes.c_double),
+        ("n_vox", ctypes.c_int64), ("n_gp", ctypes.c_int64), ("n_folded", ctypes.c_int64),
+        ("sev_raw", ctypes.c_uint64), ("folded", ctypes.c_int32), ("pad", ctypes.c_int32),
+    ]
+
+    def as_dict(self):
+        return dict(obj=np.array(self.obj[:], np.float64), severity=self.severity,
+                    s_img=self.s_img, s_guid=self.s_guid, s_mag=self.s_mag,
+                    n_vox=int(self.n_vox), n_gp=int(self.n_gp), n_folded=int(self.n_folded),
+                    sev_raw=int(self.sev_raw), folded=int(self.folded))
+
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library (gcc, -O2, no vendor code)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-std=c99", "-O2", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_SO)
+        L.orc_setup.argtypes = [ctypes.POINTER(_Problem), ctypes.POINTER(ctypes.c_void_p)]
+        L.orc_setup.restype = ctypes.c_int
+        L.orc_free.argtypes = [ctypes.c_void_p]
+        L.orc_eval.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                               ctypes.POINTER(_Result)]
+        L.orc_eval.restype = ctypes.c_int
+        L.orc_eval_tet.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                   ctypes.c_void_p]
+        L.orc_eval_partial.argtypes = [ctypes.c_void_p] + [ctypes.c_void_p] * 4 + [
+            ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(_Result), ctypes.POINTER(_Result),
+            ctypes.POINTER(ctypes.c_int32)]
+        L.orc_eval_partial.restype = ctypes.c_int
+        L.orc_n_groups.argtypes = [ctypes.c_void_p]
+        L.orc_radius.argtypes = [ctypes.c_void_p]
+        L.orc_radius.restype = ctypes.c_double
+        L.orc_oriented_tets.argtypes = [ctypes.c_void_p]
+        L.orc_oriented_tets.restype = ctypes.c_void_p
+        L.orc_distance.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
+        L.orc_distance.restype = ctypes.c_void_p
+        L.orc_snap1.argtypes = [ctypes.c_float, ctypes.c_int, ctypes.c_int]
+        L.orc_snap1.restype = ctypes.c_int64
+        L.orc_orient.argtypes = [ctypes.c_void_p] * 4
+        L.orc_orient.restype = ctypes.c_int64
+        L.orc_inside.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        L.orc_inside.restype = ctypes.c_int
+        L.orc_trilinear.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_void_p]
+        L.orc_trilinear.restype = ctypes.c_double
+        L.orc_h.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double]
+        L.orc_h.restype = ctypes.c_double
+        _lib = L
+    return _lib
+
+
+def _ptr(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+class Oracle:
+    """One registration problem set up in the oracle.
+
+    ``prob`` is any object with the attributes of ``synth.Problem`` (images,
+    topology, reference points, labels, tissue factors, guidance pairs,
+    modes).  Keyword overrides replace single attributes.
+    """
+
+    def __init__(self, prob, **override):
+        g = lambda name: override.get(name, getattr(prob, name))
+        L = lib()
+        self._keep = []
+
+        def arr(x, dt):
+            if x is None:
+                return None
+            a = np.ascontiguousarray(np.asarray(x), dtype=dt)
+            self._keep.append(a)
+            return a
+
+        img_s = arr(np.asarray(g("image_s")).astype(np.float64), np.float64)
+        img_t = arr(np.asarray(g("image_t")).astype(np.float64), np.float64)
+        nz, ny, nx = img_s.shape
+        tets = arr(g("tets"), np.int32)
+        ref = arr(g("ref_points"), np.float32)
+        lab = arr(g("tet_label"), np.int32)
+        tis = arr(g("tissue_factor"), np.float64)
+        gs = arr(g("guid_s"), np.float32)
+        gt = arr(g("guid_t"), np.float32)
+        gg = arr(g("guid_group"), np.int32)
+        n_guid = 0 if gs is None else int(gs.shape[0])
+        P = _Problem(nx=nx, ny=ny, nz=nz, pad0=0, img_s=_ptr(img_s), img_t=_ptr(img_t),
+                     n_points=int(ref.shape[0]), n_tets=int(tets.shape[0]),
+                     tets=_ptr(tets), ref_points=_ptr(ref), tet_label=_ptr(lab),
+                     tissue_factor=_ptr(tis), n_labels=0 if tis is None else int(tis.shape[0]),
+                     n_guid=n_guid, guid_s=_ptr(gs), guid_t=_ptr(gt), guid_group=_ptr(gg),
+                     trunc_radius=float(g("trunc_radius")), h_mode=int(g("h_mode")),
+                     g_mode=int(g("g_mode")), subvoxel_bits=int(g("subvoxel_bits")), pad1=0)
+        self._P = P
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.n_points = int(ref.shape[0])
+        self.n_tets = int(tets.shape[0])
+        h = ctypes.c_void_p()
+        rc = L.orc_setup(ctypes.byref(P), ctypes.byref(h))
+        if rc != 0:
+            raise OracleError(f"oracle set-up rejected the problem (code {rc})")
+        self._h = h
+        self._L = L
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            self._L.orc_free(h)
+            self._h = None
+
+    # -- queries ---------------------------------------------------------
+    @property
+    def n_groups(self) -> int:
+        return int(self._L.orc_n_groups(self._h))
+
+    @property
+    def radius(self) -> float:
+        return float(self._L.orc_radius(self._h))
+
+    def oriented_tets(self) -> np.ndarray:
+        p = self._L.orc_oriented_tets(self._h)
+        return np.ctypeslib.as_array(ctypes.cast(p, ctypes.POINTER(ctypes.c_int32)),
+                                     shape=(self.n_tets, 4)).copy()
+
+    def distance_map(self, side: int, group: int) -> np.ndarray:
+        p = self._L.orc_distance(self._h, side, group)
+        if not p:
+            raise OracleError("no distance map for that side/group")
+        return np.ctypeslib.as_array(ctypes.cast(p, ctypes.POINTER(ctypes.c_double)),
+                                     shape=(self.nz, self.ny, self.nx)).copy()
+
+    # -- evaluation ------------------------------------------------------
+    def eval(self, src, tgt, with_tets: bool = False):
+        src = np.ascontiguousarray(src, dtype=np.float32)
+        tgt = np.ascontiguousarray(tgt, dtype=np.float32)
+        recs = np.zeros(self.n_tets, TET_DTYPE) if with_tets else None
+        res = _Result()
+        rc = self._L.orc_eval(self._h, _ptr(src), _ptr(tgt), _ptr(recs), ctypes.byref(res))
+        if rc != 0:
+            raise OracleError(f"oracle eval failed ({rc})")
+        out = res.as_dict()
+        out["_raw"] = res
+        if with_tets:
+            out["tets"] = recs
+        return out
+
+    def eval_tet(self, src, tgt, t: int):
+        src = np.ascontiguousarray(src, dtype=np.float32)
+        tgt = np.ascontiguousarray(tgt, dtype=np.float32)
+        rec = np.zeros(1, TET_DTYPE)
+        self._L.orc_eval_tet(self._h, _ptr(src), _ptr(tgt), int(t), _ptr(rec))
+        return rec[0]
+
+    def eval_partial(self, old_src, old_tgt, new_src, new_tgt, changed, old_result):
+        arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in (old_src, old_tgt, new_src, new_tgt)]
+        chg = np.ascontiguousarray(changed, dtype=np.int32)
+        res = _Result()
+        na = ctypes.c_int32(0)
+        rc = self._L.orc_eval_partial(self._h, *[_ptr(a) for a in arrs], int(chg.size), _ptr(chg),
+                                      ctypes.byref(old_result["_raw"]), ctypes.byref(res),
+                                      ctypes.byref(na))
+        if rc != 0:
+            raise OracleError(f"oracle partial eval failed ({rc})")
+        out = res.as_dict()
+        out["_raw"] = res
+        out["n_affected"] = int(na.value)
+        return out
+
+
+# -- building blocks, exposed for the pins -----------------------------------
+
+def snap1(x: float, n: int, k: int) -> int:
+    return int(lib().orc_snap1(ctypes.c_float(x), n, k))
+
+
+def orient(a, b, c, d) -> int:
+    arrs = [np.ascontiguousarray(v, dtype=np.int64) for v in (a, b, c, d)]
+    return int(lib().orc_orient(*[_ptr(v) for v in arrs]))
+
+
+def inside(tet12, p) -> bool:
+    t = np.ascontiguousarray(tet12, dtype=np.int64).reshape(12)
+    q = np.ascontiguousarray(p, dtype=np.int64).reshape(3)
+    return bool(lib().orc_inside(_ptr(t), _ptr(q)))
+
+
+def trilinear(img: np.ndarray, y) -> float:
+    a = np.ascontiguousarray(img, dtype=np.float64)
+    nz, ny, nx = a.shape
+    yy = np.ascontiguousarray(y, dtype=np.float64).reshape(3)
+    return float(lib().orc_trilinear(_ptr(a), nx, ny, nz, _ptr(yy)))
+
+
+def h(mode: int, a: float, b: float) -> float:
+    return float(lib().orc_h(mode, a, b))

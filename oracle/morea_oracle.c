@@ -1,0 +1,566 @@
+/*
+ * MOREA objective oracle: a plain, slow, FP64/int64 CPU restatement of the
+ * objectives and the fold constraint of MOREA (Andreadis, Bosman,
+ * Alderliesten, GECCO 2023, arXiv 2303.04873).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the package's smoke check
+ * and the benchmark's CPU-baseline leg may load or execute this code.  The
+ * product path (the CUDA kernels behind libmorea) never calls it, and the two
+ * share no source: no headers, helpers, tables or constants.
+ *
+ * Everything is written as the plain definition: explicit loops over every
+ * voxel centre of every tetrahedron's bounding box, an exact inside test per
+ * (voxel, tet) pair, a barycentric map, an 8-corner weighted sum for the
+ * trilinear sample, sums in tet order.  No incremental evaluation, no
+ * blocking, no reordering.
+ *
+ * Paper passages followed (section / equation):
+ *   deformation magnitude  Sec. 4.1.1, f_magnitude equation; App. A.1
+ *   image intensity        Sec. 4.1.2, f_intensity and h equations; App. A.2
+ *   guidance               Sec. 4.1.3, f_guidance and g equations; App. A.3
+ *   fold constraint        Sec. 4.1.4; App. A.4 (signed-volume sign flips)
+ *   partial evaluation     Sec. 1 and Sec. 4.2.1 (re-evaluate dependent tets)
+ *
+ * Readings where the paper is silent (shared with the CUDA path by
+ * specification, not by code):
+ *   R1 snap: coordinates are clamped to the image box [-0.5, n-0.5] and
+ *      rounded half-to-even onto a grid of 2^-k voxel (k = subvoxel_bits);
+ *      q = rint((x + 0.5) * 2^k), so voxel centre i sits at (i + 1/2) 2^k.
+ *   R2 orientation: orient(a,b,c,d) = (b-a).((c-a)x(d-a)) over the integers;
+ *      tets with a negative reference volume are re-ordered (swap of the last
+ *      two vertices) so every reference sign is +; a zero reference volume is
+ *      an error.  A copy is folded iff its orient value is <= 0 (App. A.4:
+ *      a fold flips the sign; zero counts as folded).
+ *   R3 voxel association: a voxel centre belongs to a tet iff it lies inside
+ *      the tet after the symbolic perturbation p + (e, e^2, e^3), e -> 0+
+ *      (simulation of simplicity).  On a conforming, box-filling, unfolded
+ *      mesh every voxel centre is then counted exactly once (the defect the
+ *      paper attributes to the prior voxel association in App. A.2).
+ *      A folded copy is not rasterised (it contributes no voxels).
+ *   R4 trilinear sampling clamps the position to [0, n-1] per axis and uses
+ *      the cell i0 = min(floor(y), n-2).
+ *   R5 spoke edges are the four centroid-to-vertex segments.
+ *   R6 severity = sum over folded copies (both meshes) of |orient| / (6 2^3k)
+ *      (the absolute signed volume in voxel^3).
+ *   R7 guidance distance maps are exact Euclidean distances from voxel
+ *      centres to the group's contour points; mapped positions sample the
+ *      other side's map trilinearly.  Group weights |C^k|/|G| multiply as in
+ *      the printed formula.
+ *   R8 pair-transfer guidance (the prior, exact measure of App. A.3): mean of
+ *      |T(g_s) - g_t|^2 and |T'(g_t) - g_s|^2 over located points; a point
+ *      is located with R3 on its snapped coordinates.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_EINVAL 1
+#define ORC_ENOMEM 2
+
+#define ORC_MAX_GROUPS 8
+
+typedef struct { int64_t x, y, z; } orc_i3;
+
+typedef struct {
+    int32_t nx, ny, nz, pad0;
+    const double *img_s;            /* [nz][ny][nx] stored values, as double */
+    const double *img_t;
+    int32_t n_points, n_tets;
+    const int32_t *tets;            /* [T][4] */
+    const float *ref_points;        /* [V][3] */
+    const int32_t *tet_label;       /* [T] or NULL */
+    const double *tissue_factor;    /* [L] or NULL */
+    int32_t n_labels;
+    int32_t n_guid;
+    const float *guid_s;            /* [n_guid][3] */
+    const float *guid_t;
+    const int32_t *guid_group;      /* [n_guid] or NULL */
+    double trunc_radius;            /* <= 0: 2.5% of nx */
+    int32_t h_mode, g_mode, subvoxel_bits, pad1;
+} orc_problem;
+
+typedef struct {
+    double e_img[2];
+    double e_guid[2];
+    int64_t n_vox[2];
+    int64_t n_gp[2];
+    double e_mag;
+    uint64_t sev;
+    int32_t folded;                 /* bit 0: source copy, bit 1: target copy */
+    int32_t pad;
+} orc_tet;
+
+typedef struct {
+    double obj[3];                  /* f_intensity, f_magnitude, f_guidance */
+    double severity;
+    double s_img, s_guid, s_mag;
+    int64_t n_vox, n_gp, n_folded;
+    uint64_t sev_raw;
+    int32_t folded, pad;
+} orc_result;
+
+typedef struct {
+    orc_problem p;
+    int32_t *tets;                  /* positively oriented */
+    double *cdelta;                 /* elasticity factor per tet */
+    int G;
+    double wgt[ORC_MAX_GROUPS];
+    double r;
+    double *dist[2];                /* [G][N] maps of the source / target contours */
+    int64_t S;                      /* 2^k */
+} orc_state;
+
+/* ------------------------------------------------------------------ */
+/* R1: snap a coordinate onto the 2^-k voxel grid                      */
+/* ------------------------------------------------------------------ */
+static int64_t snap1(float xf, int n, int k)
+{
+    double x = (double)xf;
+    x = fmax(x, -0.5);
+    x = fmin(x, (double)n - 0.5);
+    return (int64_t)rint((x + 0.5) * ldexp(1.0, k));
+}
+
+static orc_i3 snap3(const orc_state *st, const float *pt)
+{
+    orc_i3 q;
+    q.x = snap1(pt[0], st->p.nx, st->p.subvoxel_bits);
+    q.y = snap1(pt[1], st->p.ny, st->p.subvoxel_bits);
+    q.z = snap1(pt[2], st->p.nz, st->p.subvoxel_bits);
+    return q;
+}
+
+/* R2: integer orientation determinant (six times the signed volume). */
+static int64_t orient(orc_i3 a, orc_i3 b, orc_i3 c, orc_i3 d)
+{
+    int64_t bx = b.x - a.x, by = b.y - a.y, bz = b.z - a.z;
+    int64_t cx = c.x - a.x, cy = c.y - a.y, cz = c.z - a.z;
+    int64_t dx = d.x - a.x, dy = d.y - a.y, dz = d.z - a.z;
+    return bx * (cy * dz - cz * dy) + by * (cz * dx - cx * dz) + bz * (cx * dy - cy * dx);
+}
+
+static int64_t orient_arr(const orc_i3 v[4])
+{
+    return orient(v[0], v[1], v[2], v[3]);
+}
+
+/* D_i(p): orientation with vertex i replaced by p. */
+static int64_t face_value(const orc_i3 v[4], int i, orc_i3 p)
+{
+    orc_i3 w[4];
+    memcpy(w, v, sizeof(w));
+    w[i] = p;
+    return orient_arr(w);
+}
+
+/* R3: is p inside the positively oriented tet v after the symbolic
+ * perturbation (e, e^2, e^3)?  D_i is affine in p, so
+ * D_i(p + (e, e^2, e^3)) = D_i(p) + g_x e + g_y e^2 + g_z e^3 and its sign
+ * for e -> 0+ is the first nonzero of (D_i(p), g_x, g_y, g_z). */
+static int inside_sos(const orc_i3 v[4], orc_i3 p)
+{
+    for (int i = 0; i < 4; ++i) {
+        int64_t d = face_value(v, i, p);
+        if (d > 0) continue;
+        if (d < 0) return 0;
+        orc_i3 px = p, py = p, pz = p;
+        px.x += 1; py.y += 1; pz.z += 1;
+        int64_t gx = face_value(v, i, px) - d;
+        int64_t gy = face_value(v, i, py) - d;
+        int64_t gz = face_value(v, i, pz) - d;
+        int s = gx != 0 ? (gx > 0) : gy != 0 ? (gy > 0) : (gz > 0);
+        if (!s) return 0;
+    }
+    return 1;
+}
+
+/* R4: trilinear sample as the weighted sum of the 8 cell corners. */
+static double trilinear(const double *img, int nx, int ny, int nz, const double y[3])
+{
+    int n[3] = {nx, ny, nz};
+    int i0[3];
+    double f[3];
+    for (int a = 0; a < 3; ++a) {
+        double c = fmin(fmax(y[a], 0.0), (double)(n[a] - 1));
+        int i = (int)floor(c);
+        if (i > n[a] - 2) i = n[a] - 2;
+        i0[a] = i;
+        f[a] = c - (double)i;
+    }
+    double v = 0.0;
+    for (int dz = 0; dz < 2; ++dz)
+        for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx) {
+                double w = (dx ? f[0] : 1.0 - f[0]) * (dy ? f[1] : 1.0 - f[1]) * (dz ? f[2] : 1.0 - f[2]);
+                size_t idx = ((size_t)(i0[2] + dz) * ny + (size_t)(i0[1] + dy)) * nx + (size_t)(i0[0] + dx);
+                v += w * img[idx];
+            }
+    return v;
+}
+
+/* h of Sec. 4.1.2: mode 0 = squared difference; mode 1 = the printed case
+ * split on foreground (> 0) and background (== 0) intensities. */
+static double h_fn(int mode, double a, double b)
+{
+    if (mode == 0) return (a - b) * (a - b);
+    if (a > 0.0 && b > 0.0) return (a - b) * (a - b);
+    if (a == 0.0 && b == 0.0) return 0.0;
+    return 1.0;
+}
+
+static int64_t floor_div(int64_t a, int64_t b)
+{
+    int64_t q = a / b;
+    if ((a % b != 0) && ((a < 0) != (b < 0))) --q;
+    return q;
+}
+
+static int64_t ceil_div(int64_t a, int64_t b)
+{
+    return -floor_div(-a, b);
+}
+
+/* Barycentric map of Sec. 4.2.1's dual-dynamic model: the point p of the
+ * own copy, with lambda_i = D_i(p) / D, goes to sum_i lambda_i * w_i where
+ * w_i are the other copy's vertices in voxel units. */
+static void bary_map(const orc_state *st, const orc_i3 own[4], int64_t D, const orc_i3 oth[4],
+                     orc_i3 p, double y[3])
+{
+    double S = (double)st->S;
+    y[0] = y[1] = y[2] = 0.0;
+    for (int i = 0; i < 4; ++i) {
+        double lam = (double)face_value(own, i, p) / (double)D;
+        y[0] += lam * ((double)oth[i].x / S - 0.5);
+        y[1] += lam * ((double)oth[i].y / S - 0.5);
+        y[2] += lam * ((double)oth[i].z / S - 0.5);
+    }
+}
+
+/* One side of one tet: side 0 samples source voxels in the source copy and
+ * compares with the target image at T(p); side 1 is the symmetric term with
+ * T' (the two sums of f_intensity and the two g terms of f_guidance). */
+static void eval_side(const orc_state *st, const orc_i3 own[4], const orc_i3 oth[4], int side,
+                      orc_tet *rec)
+{
+    const orc_problem *P = &st->p;
+    int64_t D = orient_arr(own);
+    if (D <= 0) return;                                /* R3: folded copy not rasterised */
+    const double *img_own = side == 0 ? P->img_s : P->img_t;
+    const double *img_oth = side == 0 ? P->img_t : P->img_s;
+    int64_t S = st->S, H = st->S / 2;
+    int n[3] = {P->nx, P->ny, P->nz};
+    int64_t lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) {
+        int64_t mn = INT64_MAX, mx = INT64_MIN;
+        for (int i = 0; i < 4; ++i) {
+            int64_t c = a == 0 ? own[i].x : a == 1 ? own[i].y : own[i].z;
+            if (c < mn) mn = c;
+            if (c > mx) mx = c;
+        }
+        lo[a] = ceil_div(mn - H, S);
+        hi[a] = floor_div(mx - H, S);
+        if (lo[a] < 0) lo[a] = 0;
+        if (hi[a] > n[a] - 1) hi[a] = n[a] - 1;
+    }
+    double e_img = 0.0, e_guid = 0.0;
+    int64_t nv = 0;
+    for (int64_t k = lo[2]; k <= hi[2]; ++k)
+        for (int64_t j = lo[1]; j <= hi[1]; ++j)
+            for (int64_t i = lo[0]; i <= hi[0]; ++i) {
+                orc_i3 p = {i * S + H, j * S + H, k * S + H};
+                if (!inside_sos(own, p)) continue;
+                double y[3];
+                bary_map(st, own, D, oth, p, y);
+                size_t idx = ((size_t)k * P->ny + (size_t)j) * P->nx + (size_t)i;
+                double a = img_own[idx];
+                double b = trilinear(img_oth, P->nx, P->ny, P->nz, y);
+                e_img += h_fn(P->h_mode, a, b);
+                nv += 1;
+                if (P->g_mode == 0) {
+                    for (int g = 0; g < st->G; ++g) {
+                        double dg = st->dist[side][(size_t)g * ((size_t)P->nx * P->ny * P->nz) + idx];
+                        if (dg < st->r) {
+                            double dm = trilinear(st->dist[1 - side] + (size_t)g * ((size_t)P->nx * P->ny * P->nz),
+                                                  P->nx, P->ny, P->nz, y);
+                            e_guid += st->wgt[g] * (st->r - dg) / st->r * (dg - dm) * (dg - dm);
+                        }
+                    }
+                }
+            }
+    int64_t ngp = 0;
+    if (P->g_mode == 1) {
+        for (int m = 0; m < P->n_guid; ++m) {
+            const float *gown = side == 0 ? P->guid_s + 3 * m : P->guid_t + 3 * m;
+            const float *goth = side == 0 ? P->guid_t + 3 * m : P->guid_s + 3 * m;
+            orc_i3 p = snap3(st, gown);
+            if (!inside_sos(own, p)) continue;
+            double y[3];
+            bary_map(st, own, D, oth, p, y);
+            double ex = y[0] - (double)goth[0], ey = y[1] - (double)goth[1], ez = y[2] - (double)goth[2];
+            e_guid += ex * ex + ey * ey + ez * ez;
+            ngp += 1;
+        }
+    }
+    rec->e_img[side] = e_img;
+    rec->e_guid[side] = e_guid;
+    rec->n_vox[side] = nv;
+    rec->n_gp[side] = ngp;
+}
+
+static double len3(double x, double y, double z)
+{
+    return sqrt(x * x + y * y + z * z);
+}
+
+/* Per-tet summands of every objective and of the fold constraint. */
+void orc_eval_tet(const orc_state *st, const float *src, const float *tgt, int t, orc_tet *rec)
+{
+    memset(rec, 0, sizeof(*rec));
+    orc_i3 qs[4], qt[4];
+    for (int i = 0; i < 4; ++i) {
+        int v = st->tets[4 * t + i];
+        qs[i] = snap3(st, src + 3 * (size_t)v);
+        qt[i] = snap3(st, tgt + 3 * (size_t)v);
+    }
+    /* Sec. 4.1.4 / App. A.4: sign flip against the (positive) reference sign */
+    int64_t Ds = orient_arr(qs), Dt = orient_arr(qt);
+    if (Ds <= 0) { rec->folded |= 1; rec->sev += (uint64_t)(Ds < 0 ? -Ds : Ds); }
+    if (Dt <= 0) { rec->folded |= 2; rec->sev += (uint64_t)(Dt < 0 ? -Dt : Dt); }
+    /* Sec. 4.1.1: 6 edges + 4 spokes (R5), c_delta (ls - lt)^2 */
+    double S = (double)st->S;
+    double e = 0.0;
+    for (int a = 0; a < 4; ++a)
+        for (int b = a + 1; b < 4; ++b) {
+            double ls = len3((qs[b].x - qs[a].x) / S, (qs[b].y - qs[a].y) / S, (qs[b].z - qs[a].z) / S);
+            double lt = len3((qt[b].x - qt[a].x) / S, (qt[b].y - qt[a].y) / S, (qt[b].z - qt[a].z) / S);
+            e += (ls - lt) * (ls - lt);
+        }
+    double cs[3] = {0, 0, 0}, ct[3] = {0, 0, 0};
+    for (int i = 0; i < 4; ++i) {
+        cs[0] += qs[i].x / 4.0; cs[1] += qs[i].y / 4.0; cs[2] += qs[i].z / 4.0;
+        ct[0] += qt[i].x / 4.0; ct[1] += qt[i].y / 4.0; ct[2] += qt[i].z / 4.0;
+    }
+    for (int i = 0; i < 4; ++i) {
+        double ls = len3((qs[i].x - cs[0]) / S, (qs[i].y - cs[1]) / S, (qs[i].z - cs[2]) / S);
+        double lt = len3((qt[i].x - ct[0]) / S, (qt[i].y - ct[1]) / S, (qt[i].z - ct[2]) / S);
+        e += (ls - lt) * (ls - lt);
+    }
+    rec->e_mag = st->cdelta[t] * e;
+    /* Sec. 4.1.2 / 4.1.3: both sampling sides */
+    eval_side(st, qs, qt, 0, rec);
+    eval_side(st, qt, qs, 1, rec);
+}
+
+static void finish(const orc_state *st, orc_result *res)
+{
+    const orc_problem *P = &st->p;
+    res->obj[0] = res->n_vox > 0 ? res->s_img / (double)res->n_vox : 0.0;
+    res->obj[1] = res->s_mag / (10.0 * (double)P->n_tets);
+    if (P->g_mode == 0)
+        res->obj[2] = res->n_vox > 0 ? res->s_guid / (double)res->n_vox : 0.0;
+    else if (P->g_mode == 1)
+        res->obj[2] = res->n_gp > 0 ? res->s_guid / (double)res->n_gp : 0.0;
+    else
+        res->obj[2] = 0.0;
+    res->folded = res->n_folded > 0;
+    double S = (double)st->S;
+    res->severity = (double)res->sev_raw / (6.0 * S * S * S);
+}
+
+static void add_rec(orc_result *res, const orc_tet *r, double sign)
+{
+    res->s_img += sign * (r->e_img[0] + r->e_img[1]);
+    res->s_guid += sign * (r->e_guid[0] + r->e_guid[1]);
+    res->s_mag += sign * r->e_mag;
+    int64_t is = sign > 0 ? 1 : -1;
+    res->n_vox += is * (r->n_vox[0] + r->n_vox[1]);
+    res->n_gp += is * (r->n_gp[0] + r->n_gp[1]);
+    res->n_folded += is * (int64_t)(((r->folded & 1) != 0) + ((r->folded & 2) != 0));
+    if (sign > 0) res->sev_raw += r->sev; else res->sev_raw -= r->sev;
+}
+
+/* Totals of f_intensity, f_magnitude, f_guidance (sums in tet order). */
+void orc_totals(const orc_state *st, const orc_tet *recs, orc_result *res)
+{
+    memset(res, 0, sizeof(*res));
+    for (int t = 0; t < st->p.n_tets; ++t) add_rec(res, &recs[t], 1.0);
+    finish(st, res);
+}
+
+/* Full evaluation of one solution (src, tgt: [V][3]). recs may be NULL. */
+int orc_eval(const orc_state *st, const float *src, const float *tgt, orc_tet *recs, orc_result *res)
+{
+    orc_tet *own = recs;
+    if (!own) {
+        own = (orc_tet *)malloc(sizeof(orc_tet) * (size_t)st->p.n_tets);
+        if (!own) return ORC_ENOMEM;
+    }
+    for (int t = 0; t < st->p.n_tets; ++t) orc_eval_tet(st, src, tgt, t, &own[t]);
+    orc_totals(st, own, res);
+    if (!recs) free(own);
+    return ORC_OK;
+}
+
+/* Partial evaluation (Sec. 1, Sec. 4.2.1): only the tets with a changed
+ * vertex are re-evaluated; result = old totals + sum(new - old). */
+int orc_eval_partial(const orc_state *st, const float *old_src, const float *old_tgt,
+                     const float *new_src, const float *new_tgt, int n_chg, const int32_t *chg,
+                     const orc_result *old_tot, orc_result *res, int32_t *n_affected)
+{
+    const orc_problem *P = &st->p;
+    char *mark = (char *)calloc((size_t)P->n_points, 1);
+    if (!mark) return ORC_ENOMEM;
+    for (int m = 0; m < n_chg; ++m) {
+        if (chg[m] < 0 || chg[m] >= P->n_points) { free(mark); return ORC_EINVAL; }
+        mark[chg[m]] = 1;
+    }
+    *res = *old_tot;
+    int32_t na = 0;
+    for (int t = 0; t < P->n_tets; ++t) {
+        const int32_t *tv = st->tets + 4 * t;
+        if (!(mark[tv[0]] || mark[tv[1]] || mark[tv[2]] || mark[tv[3]])) continue;
+        orc_tet ro, rn;
+        orc_eval_tet(st, old_src, old_tgt, t, &ro);
+        orc_eval_tet(st, new_src, new_tgt, t, &rn);
+        add_rec(res, &ro, -1.0);
+        add_rec(res, &rn, 1.0);
+        ++na;
+    }
+    free(mark);
+    finish(st, res);
+    if (n_affected) *n_affected = na;
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* set-up                                                              */
+/* ------------------------------------------------------------------ */
+
+void orc_free(orc_state *st)
+{
+    if (!st) return;
+    free(st->tets);
+    free(st->cdelta);
+    free(st->dist[0]);
+    free(st->dist[1]);
+    free(st);
+}
+
+/* R7: brute-force Euclidean distance map of one contour point set. */
+static void distance_map(const orc_problem *P, const float *pts, int g, double *out)
+{
+    for (int k = 0; k < P->nz; ++k)
+        for (int j = 0; j < P->ny; ++j)
+            for (int i = 0; i < P->nx; ++i) {
+                double best = INFINITY;
+                for (int m = 0; m < P->n_guid; ++m) {
+                    int gm = P->guid_group ? P->guid_group[m] : 0;
+                    if (gm != g) continue;
+                    double d = len3(i - (double)pts[3 * m], j - (double)pts[3 * m + 1], k - (double)pts[3 * m + 2]);
+                    if (d < best) best = d;
+                }
+                out[((size_t)k * P->ny + j) * P->nx + i] = best;
+            }
+}
+
+int orc_setup(const orc_problem *P, orc_state **out)
+{
+    *out = NULL;
+    if (P->nx < 2 || P->ny < 2 || P->nz < 2) return ORC_EINVAL;
+    if (P->subvoxel_bits < 2 || P->subvoxel_bits > 14) return ORC_EINVAL;
+    int64_t S = (int64_t)1 << P->subvoxel_bits;
+    int nmax = P->nx > P->ny ? P->nx : P->ny;
+    if (P->nz > nmax) nmax = P->nz;
+    if ((int64_t)nmax * S > ((int64_t)1 << 16)) return ORC_EINVAL;
+    if (P->n_points < 4 || P->n_tets < 1 || !P->tets || !P->ref_points) return ORC_EINVAL;
+    if (P->h_mode < 0 || P->h_mode > 1 || P->g_mode < 0 || P->g_mode > 2) return ORC_EINVAL;
+    if (P->n_guid < 0 || (P->n_guid > 0 && (!P->guid_s || !P->guid_t))) return ORC_EINVAL;
+    orc_state *st = (orc_state *)calloc(1, sizeof(orc_state));
+    if (!st) return ORC_ENOMEM;
+    st->p = *P;
+    st->S = S;
+    st->tets = (int32_t *)malloc(sizeof(int32_t) * 4 * (size_t)P->n_tets);
+    st->cdelta = (double *)malloc(sizeof(double) * (size_t)P->n_tets);
+    if (!st->tets || !st->cdelta) { orc_free(st); return ORC_ENOMEM; }
+    /* R2: positive reference orientation */
+    for (int t = 0; t < P->n_tets; ++t) {
+        orc_i3 q[4];
+        for (int i = 0; i < 4; ++i) {
+            int v = P->tets[4 * t + i];
+            if (v < 0 || v >= P->n_points) { orc_free(st); return ORC_EINVAL; }
+            st->tets[4 * t + i] = v;
+            q[i] = snap3(st, P->ref_points + 3 * (size_t)v);
+        }
+        int64_t D = orient_arr(q);
+        if (D == 0) { orc_free(st); return ORC_EINVAL; }
+        if (D < 0) {
+            int32_t tmp = st->tets[4 * t + 2];
+            st->tets[4 * t + 2] = st->tets[4 * t + 3];
+            st->tets[4 * t + 3] = tmp;
+        }
+        /* App. A.1: per-tet elasticity factor from its tissue label */
+        int lab = P->tet_label ? P->tet_label[t] : 0;
+        if (P->tissue_factor) {
+            if (lab < 0 || lab >= P->n_labels) { orc_free(st); return ORC_EINVAL; }
+            st->cdelta[t] = P->tissue_factor[lab];
+        } else {
+            st->cdelta[t] = 1.0;
+        }
+    }
+    /* guidance groups, weights |C^k| / |G| and truncation radius */
+    st->G = 0;
+    for (int m = 0; m < P->n_guid; ++m) {
+        int g = P->guid_group ? P->guid_group[m] : 0;
+        if (g < 0 || g >= ORC_MAX_GROUPS) { orc_free(st); return ORC_EINVAL; }
+        if (g + 1 > st->G) st->G = g + 1;
+    }
+    for (int g = 0; g < st->G; ++g) {
+        int cnt = 0;
+        for (int m = 0; m < P->n_guid; ++m) cnt += (P->guid_group ? P->guid_group[m] : 0) == g;
+        st->wgt[g] = (double)cnt / (double)P->n_guid;
+    }
+    st->r = P->trunc_radius > 0.0 ? P->trunc_radius : 0.025 * (double)P->nx;
+    if (P->g_mode == 0 && st->G > 0) {
+        size_t N = (size_t)P->nx * P->ny * P->nz;
+        for (int s = 0; s < 2; ++s) {
+            st->dist[s] = (double *)malloc(sizeof(double) * N * (size_t)st->G);
+            if (!st->dist[s]) { orc_free(st); return ORC_ENOMEM; }
+            for (int g = 0; g < st->G; ++g)
+                distance_map(P, s == 0 ? P->guid_s : P->guid_t, g, st->dist[s] + (size_t)g * N);
+        }
+    }
+    *out = st;
+    return ORC_OK;
+}
+
+/* accessors used by the tests */
+int orc_n_groups(const orc_state *st) { return st->G; }
+double orc_radius(const orc_state *st) { return st->r; }
+const int32_t *orc_oriented_tets(const orc_state *st) { return st->tets; }
+const double *orc_distance(const orc_state *st, int side, int g)
+{
+    if (!st->dist[side] || g < 0 || g >= st->G) return NULL;
+    return st->dist[side] + (size_t)g * ((size_t)st->p.nx * st->p.ny * st->p.nz);
+}
+
+/* Exposed building blocks, so the tests can pin them one by one. */
+int64_t orc_snap1(float x, int n, int k) { return snap1(x, n, k); }
+int64_t orc_orient(const int64_t *a, const int64_t *b, const int64_t *c, const int64_t *d)
+{
+    orc_i3 A = {a[0], a[1], a[2]}, B = {b[0], b[1], b[2]}, C = {c[0], c[1], c[2]}, D = {d[0], d[1], d[2]};
+    return orient(A, B, C, D);
+}
+int orc_inside(const int64_t *tet12, const int64_t *p3)
+{
+    orc_i3 v[4];
+    for (int i = 0; i < 4; ++i) { v[i].x = tet12[3 * i]; v[i].y = tet12[3 * i + 1]; v[i].z = tet12[3 * i + 2]; }
+    orc_i3 p = {p3[0], p3[1], p3[2]};
+    return inside_sos(v, p);
+}
+double orc_trilinear(const double *img, int nx, int ny, int nz, const double *y)
+{
+    return trilinear(img, nx, ny, nz, y);
+}
+double orc_h(int mode, double a, double b) { return h_fn(mode, a, b); }
