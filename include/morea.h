@@ -1,0 +1,240 @@
+/*
+ * morea.h -- C ABI of libmorea, a GB300 (sm_103a) evaluator for the
+ * objectives and the fold constraint of MOREA (Andreadis, Bosman,
+ * Alderliesten, "MOREA: a GPU-accelerated Evolutionary Algorithm for
+ * Multi-Objective Deformable Registration of 3D Medical Images", GECCO 2023,
+ * arXiv 2303.04873).
+ *
+ * A registration solution is a pair of tetrahedral meshes with one shared
+ * topology: one mesh on the source image I_s, one on the target image I_t
+ * (the dual-dynamic model, Sec. 1 and Sec. 4.2.1).  Each tet defines an
+ * affine map T between its source and target copies and the inverse map T'.
+ * libmorea evaluates, for a population of such solutions,
+ *   obj[0] f_intensity  (Sec. 4.1.2, equations for f_intensity and h),
+ *   obj[1] f_magnitude  (Sec. 4.1.1, f_magnitude equation; App. A.1),
+ *   obj[2] f_guidance   (Sec. 4.1.3, equations for f_guidance and g; App. A.3),
+ * and the fold constraint (Sec. 4.1.4; App. A.4), fully or by partial
+ * re-evaluation of the tets that depend on changed points (Sec. 1;
+ * Sec. 4.2.1).  All three objectives are minimised.
+ *
+ * Conventions
+ *   - Images are [nz][ny][nx], x fastest.  Coordinates are voxel-index
+ *     units: voxel (i, j, k) has its centre at (i, j, k); the image box is
+ *     [-0.5, n - 0.5] per axis.  Points are (x, y, z) float triples.
+ *   - Every coordinate is clamped to the image box and snapped, round half
+ *     to even, onto a grid of 2^-k voxel (k = subvoxel_bits).  On that grid
+ *     orientation determinants are exact, so coverage counts and fold flags
+ *     are exact integers.
+ *   - A voxel centre belongs to a tet iff it is inside the tet after the
+ *     symbolic perturbation (e, e^2, e^3), e -> 0+.  On a conforming,
+ *     box-filling, unfolded mesh every voxel centre is counted exactly once.
+ *     A folded tet copy (orientation <= 0) is not rasterised.
+ *   - "stream" is a cudaStream_t (NULL = legacy default stream).  Every
+ *     evaluation call only enqueues work on that stream: it does not
+ *     synchronise and does not allocate memory.  All memory a problem needs
+ *     is allocated by morea_create_problem.
+ *   - Pointers documented "device" must be device (or managed) memory of the
+ *     current device; "host" pointers are read before the call returns.
+ *     The caller owns every pointer it passes; the handle owns its copies.
+ *   - Argument errors are found on the host before anything is enqueued and
+ *     return MOREA_EINVAL with nothing launched.  Errors that only the GPU
+ *     can see (a point id out of range in a partial request, a request longer
+ *     than max_changed, a scratch overflow) set bits in a device status word
+ *     of the problem; the request's outputs become NaN / folded = 1, and
+ *     morea_device_status returns and clears the word.  No kernel traps.
+ */
+#ifndef MOREA_H
+#define MOREA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum morea_status {
+    MOREA_OK = 0,
+    MOREA_EINVAL = 1,      /* invalid argument or problem description */
+    MOREA_ENOMEM = 2,      /* device or host allocation failed (create only) */
+    MOREA_ECUDA = 3,       /* a CUDA runtime call failed */
+    MOREA_ETIMEOUT = 4,    /* a bounded device-side wait gave up */
+    MOREA_ENOTIMPL = 5,    /* option not implemented */
+    MOREA_EDEVICE = 6      /* the device status word reported bad input */
+} morea_status;
+
+typedef enum morea_dtype { MOREA_F32 = 0, MOREA_F16 = 1 } morea_dtype;
+
+/* h of Sec. 4.1.2.  PLAIN_SSD: (a - b)^2.  MOREA_FG: the printed case split:
+ * (a - b)^2 if a > 0 and b > 0; 0 if a == 0 and b == 0; 1 otherwise, with
+ * a the stored voxel value and b the trilinear sample of the other image. */
+typedef enum morea_hmode { MOREA_H_PLAIN_SSD = 0, MOREA_H_MOREA_FG = 1 } morea_hmode;
+
+/* CONTINUOUS: the distance-map formulation of Sec. 4.1.3 / App. A.3.
+ * PAIR_TRANSFER: the exact measure of the prior work described in App. A.3:
+ * mean of |T(g_s) - g_t|^2 and |T'(g_t) - g_s|^2 over located points.
+ * OFF: f_guidance = 0. */
+typedef enum morea_gmode {
+    MOREA_G_CONTINUOUS = 0, MOREA_G_PAIR_TRANSFER = 1, MOREA_G_OFF = 2
+} morea_gmode;
+
+/* Bits of the device status word. */
+#define MOREA_DEV_BAD_POINT     0x1u   /* partial request names a point id out of range */
+#define MOREA_DEV_TOO_MANY      0x2u   /* partial request longer than max_changed / bad offsets */
+#define MOREA_DEV_DUPLICATE     0x4u   /* partial request lists a point twice */
+#define MOREA_DEV_OVERFLOW      0x8u   /* affected-tet scratch overflow */
+#define MOREA_DEV_BAD_SLOT      0x10u  /* slot index out of range */
+#define MOREA_DEV_TIMEOUT       0x20u  /* bounded wait gave up */
+
+typedef struct morea_problem morea_problem;            /* opaque handle */
+
+/* Problem description (Sec. 4.1).  Read during morea_create_problem only. */
+typedef struct morea_problem_desc {
+    int32_t nx, ny, nz;            /* image extent, each >= 2 */
+    int32_t dtype;                 /* morea_dtype of both images */
+    const void *image_s;           /* source image I_s, [nz][ny][nx], host or device */
+    const void *image_t;           /* target image I_t, same layout */
+    int32_t n_points, n_tets;      /* V >= 4, T >= 1 */
+    const int32_t *tets;           /* host [T][4] vertex ids, shared topology */
+    const float *ref_points;       /* host [V][3] initial mesh: gives the reference signs */
+    const int32_t *tet_label;      /* host [T] tissue label per tet, or NULL (all 0) */
+    const double *tissue_factor;   /* host [n_labels] elasticity factor per label, or NULL (1.0) */
+    int32_t n_labels;
+    int32_t n_guid;                /* number of guidance point pairs (>= 0) */
+    const float *guid_s;           /* host [n_guid][3] contour points on I_s */
+    const float *guid_t;           /* host [n_guid][3] corresponding points on I_t */
+    const int32_t *guid_group;     /* host [n_guid] contour-group id in [0, 8), or NULL (all 0) */
+    double trunc_radius;           /* guidance truncation radius r in voxels; <= 0: 0.025 * nx */
+    int32_t h_mode;                /* morea_hmode */
+    int32_t g_mode;                /* morea_gmode */
+    int32_t subvoxel_bits;         /* k in [2, 14] with max(nx, ny, nz) * 2^k <= 65536; 0: 8 */
+    int32_t max_solutions;         /* number of cache slots (solutions kept resident) >= 1 */
+    int32_t max_requests;          /* largest n_req of morea_eval_partial (0: max_solutions) */
+    int32_t max_changed;           /* largest changed-point count of one request (0: 64) */
+} morea_problem_desc;
+
+/* Per-(slot, tet) summands kept by the handle (what a partial evaluation
+ * subtracts and adds).  Index 0 = source side (voxels of I_s in the source
+ * copy), 1 = target side. */
+typedef struct morea_tet_record {
+    float e_img[2];       /* sum of h over the tet copy's voxel centres */
+    float e_guid[2];      /* continuous: weighted sum of g terms; pair: sum of squared transfer errors */
+    int32_t n_vox[2];     /* voxel centres associated with the tet copy (exact) */
+    int32_t n_gp[2];      /* guidance points located in the copy (pair mode) */
+    float e_mag;          /* c_delta * sum over the 10 edges of (|e_s| - |e_t|)^2 */
+    uint32_t folded;      /* bit 0: source copy folded, bit 1: target copy folded */
+    uint64_t sev;         /* sum of |orient| over folded copies (integer, 6 * 2^3k * voxel^3) */
+} morea_tet_record;
+
+/* Per-slot totals over all tets (FP64 sums, exact integer counts). */
+typedef struct morea_totals {
+    double s_img, s_guid, s_mag;
+    int64_t n_vox, n_gp, n_folded;
+    uint64_t sev;
+    int64_t reserved;
+} morea_totals;
+
+/* Create a problem: validates the description, copies the images to the
+ * device, orients every tet positively against ref_points (a zero reference
+ * volume is MOREA_EINVAL), builds the vertex-to-tet adjacency, computes the
+ * guidance distance maps (Sec. 4.1.3) and allocates the per-slot caches and
+ * all scratch.  Synchronises `stream` before returning.
+ * On error *out is NULL and nothing is leaked. */
+morea_status morea_create_problem(const morea_problem_desc *desc, void *stream,
+                                  morea_problem **out);
+
+/* Frees everything the handle owns (synchronises the device first).  NULL is a no-op. */
+morea_status morea_destroy_problem(morea_problem *p);
+
+/* Full evaluation (Sec. 4.1) of n_sol solutions.
+ *   slot      device [n_sol] cache slot of each solution in [0, max_solutions),
+ *             distinct within a call, or NULL for slots 0..n_sol-1
+ *   src_pts   device [n_sol][V][3] source-mesh points
+ *   tgt_pts   device [n_sol][V][3] target-mesh points
+ *   obj       device [n_sol][3] out: f_intensity, f_magnitude, f_guidance
+ *   folded    device [n_sol] out: 1 if any tet copy of either mesh is folded
+ *   severity  device [n_sol] out, or NULL: sum of |signed volume| (voxel^3) of folded copies
+ * The slots' coordinates, per-tet records and totals are replaced, so later
+ * partial evaluations start from these solutions. */
+morea_status morea_eval_full(morea_problem *p, int32_t n_sol, const int32_t *slot,
+                             const float *src_pts, const float *tgt_pts,
+                             double *obj, uint8_t *folded, double *severity, void *stream);
+
+/* Partial evaluation (Sec. 1; Sec. 4.2.1): request r moves the points
+ * chg_pts[chg_off[r] .. chg_off[r+1]) of the solution in slot[r] to
+ * chg_src / chg_tgt (absolute coordinates, aligned with chg_pts).  Only
+ * the tets incident to a moved point are re-evaluated; the result is the
+ * slot's totals plus the sum over those tets of (new - cached).
+ *   slot      device [n_req]
+ *   chg_off   device [n_req + 1], non-decreasing, chg_off[0] = 0
+ *   chg_pts   device [chg_off[n_req]] point ids, distinct within a request,
+ *             at most max_changed per request
+ *   chg_src   device [chg_off[n_req]][3]
+ *   chg_tgt   device [chg_off[n_req]][3]
+ *   obj, folded, severity  as in morea_eval_full, per request (severity may be NULL)
+ *   commit    device [n_req] or NULL: nonzero commits the request into its
+ *             slot right away (same as morea_commit_partial afterwards)
+ * n_req <= max_requests.  Requests on the same slot are evaluated against
+ * the slot's state before the call; if several of them are committed their
+ * affected tets must be disjoint.  The scratch of this call stays valid for
+ * morea_commit_partial until the next morea_eval_partial on the handle. */
+morea_status morea_eval_partial(morea_problem *p, int32_t n_req, const int32_t *slot,
+                                const int32_t *chg_off, const int32_t *chg_pts,
+                                const float *chg_src, const float *chg_tgt,
+                                double *obj, uint8_t *folded, double *severity,
+                                const uint8_t *commit, void *stream);
+
+/* Commit the requests of the last morea_eval_partial whose accept[r] is
+ * nonzero (accept: device [n_req], n_req equal to that call's).  This is the
+ * acceptance step of optimal mixing (Sec. 3): an accepted partial solution
+ * replaces its parent in the slot. */
+morea_status morea_commit_partial(morea_problem *p, int32_t n_req, const uint8_t *accept,
+                                  void *stream);
+
+/* Fold constraint only (Sec. 4.1.4; App. A.4) for n_sol solutions, without
+ * touching any slot: folded [n_sol] and severity [n_sol] (may be NULL), device. */
+morea_status morea_check_folds(morea_problem *p, int32_t n_sol, const float *src_pts,
+                               const float *tgt_pts, uint8_t *folded, double *severity,
+                               void *stream);
+
+/* Copy the cached per-tet records of n_sol slots (device [n_sol], or NULL
+ * for 0..n_sol-1) into out (device [n_sol][T]), tets in the problem's order. */
+morea_status morea_read_records(morea_problem *p, int32_t n_sol, const int32_t *slot,
+                                morea_tet_record *out, void *stream);
+
+/* Copy the totals of n_sol slots into out (device [n_sol]). */
+morea_status morea_read_totals(morea_problem *p, int32_t n_sol, const int32_t *slot,
+                               morea_totals *out, void *stream);
+
+/* Synchronise `stream`, return and clear the device status word (bits
+ * MOREA_DEV_*) in *bits; returns MOREA_EDEVICE if any bit was set. */
+morea_status morea_device_status(morea_problem *p, void *stream, uint32_t *bits);
+
+/* Problem sizes after creation: n_points, n_tets, number of guidance
+ * groups, truncation radius and subvoxel_bits in use (any output may be NULL). */
+morea_status morea_problem_info(const morea_problem *p, int32_t *n_points, int32_t *n_tets,
+                                int32_t *n_groups, double *trunc_radius, int32_t *subvoxel_bits);
+
+/* Instrumentation for benchmarks (not a step of the method; the paper has no
+ * counterpart).  flags bit 0: record a CUDA event pair on the call's stream
+ * around every launch of the rasterisation/sampling kernel (the hot loop);
+ * bit 1: after each such launch, count the voxel visits it made (one extra
+ * small kernel, outside the event pair).  flags = 0 turns both off.  Every
+ * call resets the accumulated figures.  Creates CUDA events on first use; no
+ * device memory is allocated. */
+morea_status morea_profile(morea_problem *p, uint32_t flags);
+
+/* Synchronise the events recorded since the last morea_profile call and
+ * return the summed kernel time in ms, the number of timed launches and the
+ * counted voxel visits (any output may be NULL). */
+morea_status morea_profile_read(morea_problem *p, double *raster_ms, int64_t *launches,
+                                int64_t *visits);
+
+/* Static description of a status code. */
+const char *morea_status_string(morea_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MOREA_H */

@@ -49,6 +49,12 @@
  *   R8 pair-transfer guidance (the prior, exact measure of App. A.3): mean of
  *      |T(g_s) - g_t|^2 and |T'(g_t) - g_s|^2 over located points; a point
  *      is located with R3 on its snapped coordinates.
+ *   R9 h in the foreground/background mode jumps at b = 0 (from (a-b)^2 to
+ *      1), so which case applies is a decision taken by floating point.  The
+ *      oracle takes it in the GPU kernel's precision: b is recomputed in FP32
+ *      (affine map t0 + M (p - s0) with M = F adj(E) / D rounded to float,
+ *      clamped cell, fused multiply-add lerps) and only its comparison with
+ *      0 is used; the value (a - b)^2 itself is the FP64 sample.
  */
 #include <math.h>
 #include <stdint.h>
@@ -201,13 +207,69 @@ static double trilinear(const double *img, int nx, int ny, int nz, const double 
 }
 
 /* h of Sec. 4.1.2: mode 0 = squared difference; mode 1 = the printed case
- * split on foreground (> 0) and background (== 0) intensities. */
-static double h_fn(int mode, double a, double b)
+ * split on foreground (> 0) and background (== 0) intensities.  b_case is
+ * the value the case split looks at (R9), b the value that is compared. */
+static double h_case(int mode, double a, double b, double b_case)
 {
     if (mode == 0) return (a - b) * (a - b);
-    if (a > 0.0 && b > 0.0) return (a - b) * (a - b);
-    if (a == 0.0 && b == 0.0) return 0.0;
+    if (a > 0.0 && b_case > 0.0) return (a - b) * (a - b);
+    if (a == 0.0 && b_case == 0.0) return 0.0;
     return 1.0;
+}
+
+static double h_fn(int mode, double a, double b)
+{
+    return h_case(mode, a, b, b);
+}
+
+/* R9: the FP32 sample of the other image at the image of voxel (i, j, k),
+ * used only to decide the case of h in mode 1. */
+static float sample_fp32_case(const orc_state *st, const orc_i3 own[4], const orc_i3 oth[4], int64_t D,
+                              const double *img, int64_t i, int64_t j, int64_t k)
+{
+    const orc_problem *P = &st->p;
+    int64_t e[3][3], f[3][3];
+    for (int m = 0; m < 3; ++m) {
+        e[m][0] = own[m + 1].x - own[0].x; e[m][1] = own[m + 1].y - own[0].y; e[m][2] = own[m + 1].z - own[0].z;
+        f[m][0] = oth[m + 1].x - oth[0].x; f[m][1] = oth[m + 1].y - oth[0].y; f[m][2] = oth[m + 1].z - oth[0].z;
+    }
+    int64_t r[3][3];                     /* rows of adj(E): e2 x e3, e3 x e1, e1 x e2 */
+    for (int m = 0; m < 3; ++m) {
+        const int64_t *u = e[(m + 1) % 3], *v = e[(m + 2) % 3];
+        r[m][0] = u[1] * v[2] - u[2] * v[1];
+        r[m][1] = u[2] * v[0] - u[0] * v[2];
+        r[m][2] = u[0] * v[1] - u[1] * v[0];
+    }
+    const double invD = 1.0 / (double)D;
+    float M[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            M[a][b] = (float)((double)(f[0][a] * r[0][b] + f[1][a] * r[1][b] + f[2][a] * r[2][b]) * invD);
+    const float inv_s = 1.0f / (float)st->S;
+    const float s0[3] = {(float)own[0].x * inv_s - 0.5f, (float)own[0].y * inv_s - 0.5f,
+                         (float)own[0].z * inv_s - 0.5f};
+    const float t0[3] = {(float)oth[0].x * inv_s - 0.5f, (float)oth[0].y * inv_s - 0.5f,
+                         (float)oth[0].z * inv_s - 0.5f};
+    const float d[3] = {(float)i - s0[0], (float)j - s0[1], (float)k - s0[2]};
+    const int n[3] = {P->nx, P->ny, P->nz};
+    float c[3], fr[3];
+    int i0[3];
+    for (int a = 0; a < 3; ++a) {
+        float y = fmaf(M[a][0], d[0], fmaf(M[a][1], d[1], fmaf(M[a][2], d[2], t0[a])));
+        c[a] = fminf(fmaxf(y, 0.0f), (float)(n[a] - 1));
+        i0[a] = (int)c[a];
+        if (i0[a] > n[a] - 2) i0[a] = n[a] - 2;
+        fr[a] = c[a] - (float)i0[a];
+    }
+    const size_t sy = (size_t)P->nx, sz = (size_t)P->nx * P->ny;
+    const size_t b0 = ((size_t)i0[2] * P->ny + (size_t)i0[1]) * P->nx + (size_t)i0[0];
+    float v[8];
+    for (int q = 0; q < 8; ++q)
+        v[q] = (float)img[b0 + (q & 1) + ((q >> 1) & 1) * sy + ((q >> 2) & 1) * sz];
+    const float c00 = fmaf(fr[0], v[1] - v[0], v[0]), c10 = fmaf(fr[0], v[3] - v[2], v[2]);
+    const float c01 = fmaf(fr[0], v[5] - v[4], v[4]), c11 = fmaf(fr[0], v[7] - v[6], v[6]);
+    const float c0 = fmaf(fr[1], c10 - c00, c00), c1 = fmaf(fr[1], c11 - c01, c01);
+    return fmaf(fr[2], c1 - c0, c0);
 }
 
 static int64_t floor_div(int64_t a, int64_t b)
@@ -276,7 +338,8 @@ static void eval_side(const orc_state *st, const orc_i3 own[4], const orc_i3 oth
                 size_t idx = ((size_t)k * P->ny + (size_t)j) * P->nx + (size_t)i;
                 double a = img_own[idx];
                 double b = trilinear(img_oth, P->nx, P->ny, P->nz, y);
-                e_img += h_fn(P->h_mode, a, b);
+                double b_case = P->h_mode == 1 ? (double)sample_fp32_case(st, own, oth, D, img_oth, i, j, k) : b;
+                e_img += h_case(P->h_mode, a, b, b_case);
                 nv += 1;
                 if (P->g_mode == 0) {
                     for (int g = 0; g < st->G; ++g) {

@@ -1,0 +1,324 @@
+"""ctypes binding of libmorea (include/morea.h): argument marshalling only.
+
+Every step of the evaluation runs in the library's CUDA kernels; this module
+checks tensor shapes, dtypes and devices, passes raw pointers and the current
+torch CUDA stream, and turns status codes into exceptions.  PyTorch supplies
+device memory and streams.  There is no CPU path: if ``libmorea.so`` is not
+built, importing this module fails.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libmorea.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTIMPL, EDEVICE = range(7)
+F32, F16 = 0, 1
+H_PLAIN_SSD, H_MOREA_FG = 0, 1
+G_CONTINUOUS, G_PAIR_TRANSFER, G_OFF = 0, 1, 2
+
+DEV_BAD_POINT = 0x1
+DEV_TOO_MANY = 0x2
+DEV_DUPLICATE = 0x4
+DEV_OVERFLOW = 0x8
+DEV_BAD_SLOT = 0x10
+DEV_TIMEOUT = 0x20
+
+# exported entry points, in header order (checked by the tests against include/morea.h)
+ENTRY_POINTS = (
+    "morea_create_problem", "morea_destroy_problem", "morea_eval_full", "morea_eval_partial",
+    "morea_commit_partial", "morea_check_folds", "morea_read_records", "morea_read_totals",
+    "morea_device_status", "morea_problem_info", "morea_profile", "morea_profile_read",
+    "morea_status_string",
+)
+
+TET_RECORD_DTYPE = np.dtype([
+    ("e_img", "<f4", (2,)), ("e_guid", "<f4", (2,)), ("n_vox", "<i4", (2,)), ("n_gp", "<i4", (2,)),
+    ("e_mag", "<f4"), ("folded", "<u4"), ("sev", "<u8"),
+])
+TOTALS_DTYPE = np.dtype([
+    ("s_img", "<f8"), ("s_guid", "<f8"), ("s_mag", "<f8"), ("n_vox", "<i8"), ("n_gp", "<i8"),
+    ("n_folded", "<i8"), ("sev", "<u8"), ("reserved", "<i8"),
+])
+
+
+class MoreaError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {status_string(code)} ({code})")
+
+
+class ProblemDesc(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32), ("dtype", ctypes.c_int32),
+        ("image_s", ctypes.c_void_p), ("image_t", ctypes.c_void_p),
+        ("n_points", ctypes.c_int32), ("n_tets", ctypes.c_int32),
+        ("tets", ctypes.c_void_p), ("ref_points", ctypes.c_void_p), ("tet_label", ctypes.c_void_p),
+        ("tissue_factor", ctypes.c_void_p), ("n_labels", ctypes.c_int32), ("n_guid", ctypes.c_int32),
+        ("guid_s", ctypes.c_void_p), ("guid_t", ctypes.c_void_p), ("guid_group", ctypes.c_void_p),
+        ("trunc_radius", ctypes.c_double), ("h_mode", ctypes.c_int32), ("g_mode", ctypes.c_int32),
+        ("subvoxel_bits", ctypes.c_int32), ("max_solutions", ctypes.c_int32),
+        ("max_requests", ctypes.c_int32), ("max_changed", ctypes.c_int32),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """Load libmorea.so (built in-tree by ``paper_2303_04873_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libmorea.so is not built ({LIB_PATH}); run paper_2303_04873_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, u8p = ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p
+    L.morea_create_problem.argtypes = [ctypes.POINTER(ProblemDesc), vp, ctypes.POINTER(vp)]
+    L.morea_destroy_problem.argtypes = [vp]
+    L.morea_eval_full.argtypes = [vp, i32, vp, vp, vp, vp, u8p, vp, vp]
+    L.morea_eval_partial.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, u8p, vp, u8p, vp]
+    L.morea_commit_partial.argtypes = [vp, i32, u8p, vp]
+    L.morea_check_folds.argtypes = [vp, i32, vp, vp, u8p, vp, vp]
+    L.morea_read_records.argtypes = [vp, i32, vp, vp, vp]
+    L.morea_read_totals.argtypes = [vp, i32, vp, vp, vp]
+    L.morea_device_status.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_uint32)]
+    L.morea_problem_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)]
+    L.morea_profile.argtypes = [vp, ctypes.c_uint32]
+    L.morea_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
+                                     ctypes.POINTER(ctypes.c_int64)]
+    L.morea_status_string.argtypes = [i32]
+    L.morea_status_string.restype = ctypes.c_char_p
+    for name in ENTRY_POINTS:
+        if name != "morea_status_string":
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def status_string(code: int) -> str:
+    return lib().morea_status_string(int(code)).decode()
+
+
+def _check(code: int, what: str):
+    if code != OK:
+        raise MoreaError(code, what)
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _dev(t: Optional[torch.Tensor], dtype, shape=None, name="tensor"):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host(a, dtype):
+    return np.ascontiguousarray(np.asarray(a), dtype=dtype)
+
+
+class Problem:
+    """A registration problem resident on the current CUDA device.
+
+    ``prob`` is any object with the attributes of ``synth.Problem`` (images,
+    topology, reference points, labels, tissue factors, guidance pairs,
+    modes).  Keyword overrides replace single attributes.
+    """
+
+    def __init__(self, prob, max_solutions: Optional[int] = None, max_requests: int = 0,
+                 max_changed: int = 64, stream=None, **override):
+        g = lambda name: override.get(name, getattr(prob, name))
+        L = lib()
+        keep = []
+
+        def host(x, dt):
+            if x is None:
+                return None
+            a = _host(x, dt)
+            keep.append(a)
+            return a
+
+        img_s = np.ascontiguousarray(np.asarray(g("image_s")))
+        img_t = np.ascontiguousarray(np.asarray(g("image_t")))
+        if img_s.dtype == np.float16:
+            dtype = F16
+        else:
+            img_s = img_s.astype(np.float32)
+            img_t = img_t.astype(np.float32)
+            dtype = F32
+        img_t = img_t.astype(img_s.dtype)
+        keep += [img_s, img_t]
+        nz, ny, nx = img_s.shape
+        tets = host(g("tets"), np.int32)
+        ref = host(g("ref_points"), np.float32)
+        lab = host(g("tet_label"), np.int32)
+        tis = host(g("tissue_factor"), np.float64)
+        gs = host(g("guid_s"), np.float32)
+        gt = host(g("guid_t"), np.float32)
+        gg = host(g("guid_group"), np.int32)
+        n_guid = 0 if gs is None else int(gs.shape[0])
+        if max_solutions is None:
+            sol = override.get("sol_src", getattr(prob, "sol_src", None))
+            max_solutions = int(sol.shape[0]) if sol is not None else 1
+        ptr = lambda a: None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+        desc = ProblemDesc(
+            nx=nx, ny=ny, nz=nz, dtype=dtype, image_s=ptr(img_s), image_t=ptr(img_t),
+            n_points=int(ref.shape[0]), n_tets=int(tets.shape[0]), tets=ptr(tets), ref_points=ptr(ref),
+            tet_label=ptr(lab), tissue_factor=ptr(tis), n_labels=0 if tis is None else int(tis.shape[0]),
+            n_guid=n_guid, guid_s=ptr(gs), guid_t=ptr(gt), guid_group=ptr(gg),
+            trunc_radius=float(g("trunc_radius")), h_mode=int(g("h_mode")), g_mode=int(g("g_mode")),
+            subvoxel_bits=int(g("subvoxel_bits")), max_solutions=int(max_solutions),
+            max_requests=int(max_requests), max_changed=int(max_changed))
+        h = ctypes.c_void_p()
+        _check(L.morea_create_problem(ctypes.byref(desc), _stream(stream), ctypes.byref(h)),
+               "morea_create_problem")
+        self._h = h
+        self._L = L
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.dtype = dtype
+        nv, nt, ng, kb = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        rr = ctypes.c_double()
+        _check(L.morea_problem_info(h, ctypes.byref(nv), ctypes.byref(nt), ctypes.byref(ng), ctypes.byref(rr),
+                                    ctypes.byref(kb)), "morea_problem_info")
+        self.n_points, self.n_tets, self.n_groups = nv.value, nt.value, ng.value
+        self.trunc_radius, self.subvoxel_bits = rr.value, kb.value
+        self.max_solutions = int(max_solutions)
+        self.max_requests = int(max_requests) if max_requests else int(max_solutions)
+        self.max_changed = int(max_changed)
+        self.h_mode, self.g_mode = int(g("h_mode")), int(g("g_mode"))
+
+    # -- lifetime -----------------------------------------------------------
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _check(self._L.morea_destroy_problem(h), "morea_destroy_problem")
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        return self._h
+
+    # -- evaluation ---------------------------------------------------------
+    def eval_full(self, src: torch.Tensor, tgt: torch.Tensor, slots: Optional[torch.Tensor] = None,
+                  out=None, stream=None):
+        """Full evaluation; returns (obj [n,3] f64, folded [n] u8, severity [n] f64) on the device."""
+        n = int(src.shape[0])
+        V = self.n_points
+        dev = src.device
+        obj, folded, sev = out if out is not None else (
+            torch.empty((n, 3), dtype=torch.float64, device=dev),
+            torch.empty((n,), dtype=torch.uint8, device=dev),
+            torch.empty((n,), dtype=torch.float64, device=dev))
+        _check(self._L.morea_eval_full(
+            self._h, n, _dev(slots, torch.int32, (n,), "slots"),
+            _dev(src, torch.float32, (n, V, 3), "src"), _dev(tgt, torch.float32, (n, V, 3), "tgt"),
+            _dev(obj, torch.float64, (n, 3), "obj"), _dev(folded, torch.uint8, (n,), "folded"),
+            _dev(sev, torch.float64, (n,), "severity"), _stream(stream)), "morea_eval_full")
+        return obj, folded, sev
+
+    def eval_partial(self, slots: torch.Tensor, chg_off: torch.Tensor, chg_pts: torch.Tensor,
+                     chg_src: torch.Tensor, chg_tgt: torch.Tensor, commit: Optional[torch.Tensor] = None,
+                     out=None, stream=None):
+        """Partial evaluation of ``len(slots)`` requests; returns (obj, folded, severity)."""
+        n = int(slots.shape[0])
+        c = int(chg_pts.shape[0])
+        dev = slots.device
+        obj, folded, sev = out if out is not None else (
+            torch.empty((n, 3), dtype=torch.float64, device=dev),
+            torch.empty((n,), dtype=torch.uint8, device=dev),
+            torch.empty((n,), dtype=torch.float64, device=dev))
+        _check(self._L.morea_eval_partial(
+            self._h, n, _dev(slots, torch.int32, (n,), "slots"), _dev(chg_off, torch.int32, (n + 1,), "chg_off"),
+            _dev(chg_pts, torch.int32, (c,), "chg_pts"), _dev(chg_src, torch.float32, (c, 3), "chg_src"),
+            _dev(chg_tgt, torch.float32, (c, 3), "chg_tgt"), _dev(obj, torch.float64, (n, 3), "obj"),
+            _dev(folded, torch.uint8, (n,), "folded"), _dev(sev, torch.float64, (n,), "severity"),
+            _dev(commit, torch.uint8, (n,), "commit"), _stream(stream)), "morea_eval_partial")
+        return obj, folded, sev
+
+    def commit_partial(self, accept: torch.Tensor, stream=None):
+        n = int(accept.shape[0])
+        _check(self._L.morea_commit_partial(self._h, n, _dev(accept, torch.uint8, (n,), "accept"),
+                                            _stream(stream)), "morea_commit_partial")
+
+    def check_folds(self, src: torch.Tensor, tgt: torch.Tensor, stream=None):
+        n = int(src.shape[0])
+        V = self.n_points
+        folded = torch.empty((n,), dtype=torch.uint8, device=src.device)
+        sev = torch.empty((n,), dtype=torch.float64, device=src.device)
+        _check(self._L.morea_check_folds(
+            self._h, n, _dev(src, torch.float32, (n, V, 3), "src"), _dev(tgt, torch.float32, (n, V, 3), "tgt"),
+            _dev(folded, torch.uint8, (n,), "folded"), _dev(sev, torch.float64, (n,), "severity"),
+            _stream(stream)), "morea_check_folds")
+        return folded, sev
+
+    def read_records(self, n: int, slots: Optional[torch.Tensor] = None, stream=None) -> np.ndarray:
+        """Per-(slot, tet) cached records as a numpy structured array [n][T]."""
+        buf = torch.empty((n, self.n_tets, TET_RECORD_DTYPE.itemsize), dtype=torch.uint8, device="cuda")
+        _check(self._L.morea_read_records(self._h, n, _dev(slots, torch.int32, (n,), "slots"),
+                                          ctypes.c_void_p(buf.data_ptr()), _stream(stream)),
+               "morea_read_records")
+        return buf.cpu().numpy().view(TET_RECORD_DTYPE).reshape(n, self.n_tets)
+
+    def read_totals(self, n: int, slots: Optional[torch.Tensor] = None, stream=None) -> np.ndarray:
+        buf = torch.empty((n, TOTALS_DTYPE.itemsize), dtype=torch.uint8, device="cuda")
+        _check(self._L.morea_read_totals(self._h, n, _dev(slots, torch.int32, (n,), "slots"),
+                                         ctypes.c_void_p(buf.data_ptr()), _stream(stream)),
+               "morea_read_totals")
+        return buf.cpu().numpy().view(TOTALS_DTYPE).reshape(n)
+
+    def device_status(self, stream=None) -> int:
+        bits = ctypes.c_uint32(0)
+        rc = self._L.morea_device_status(self._h, _stream(stream), ctypes.byref(bits))
+        if rc not in (OK, EDEVICE):
+            _check(rc, "morea_device_status")
+        return int(bits.value)
+
+    # -- instrumentation ----------------------------------------------------
+    def profile(self, flags: int):
+        """bit 0: time every launch of the hot kernel with CUDA events; bit 1: count voxel visits."""
+        _check(self._L.morea_profile(self._h, int(flags)), "morea_profile")
+
+    def profile_read(self):
+        ms, n, v = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
+        _check(self._L.morea_profile_read(self._h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(v)),
+               "morea_profile_read")
+        return ms.value, n.value, v.value
+
+
+def requests_to_device(rd, device="cuda"):
+    """Move one round of partial requests (numpy dict) to device tensors."""
+    return {k: torch.as_tensor(np.ascontiguousarray(v)).to(device) for k, v in rd.items()}
