@@ -230,6 +230,44 @@ morea_status morea_profile(morea_problem *p, uint32_t flags);
 morea_status morea_profile_read(morea_problem *p, double *raster_ms, int64_t *launches,
                                 int64_t *visits);
 
+/* Largest n_sol * n_tets that morea_fold_magnitude_noalloc accepts (its
+ * fixed scratch holds one 16-byte record per (solution, tet): 8 MiB). */
+#define MOREA_NOALLOC_MAX_TET_EVALS 524288
+
+/* Fold constraint and deformation magnitude of n_sol solutions without a
+ * problem handle and without allocating any memory.  The paper has no
+ * counterpart to this entry point; it exists for callers that cannot call
+ * cudaMalloc -- code running inside another allocator or memory pool that
+ * must not re-enter it, or environments that only hand out pre-sized buffers
+ * -- and so cannot create a problem handle either.
+ *   tets        device [n_tets][4] vertex ids in [0, n_points) (any
+ *               orientation: a tet whose reference volume is negative is
+ *               re-ordered, as at problem creation; the reference volume must
+ *               be nonzero).  A tet with an id out of range is not read: its
+ *               solution gets f_mag = NaN and folded = 1.
+ *   ref_points  device [n_points][3] initial mesh (gives the reference signs)
+ *   cdelta      device [n_tets] elasticity factor of each tet
+ *   nx, ny, nz, subvoxel_bits   image box and snapping grid, as in
+ *               morea_problem_desc (subvoxel_bits 0 means 8)
+ *   src_pts, tgt_pts  device [n_sol][n_points][3]
+ *   f_mag       device [n_sol] out: f_magnitude (obj[1] of morea_eval_full)
+ *   folded      device [n_sol] out; severity device [n_sol] out or NULL
+ * The per-(solution, tet) intermediates go to one fixed device array inside
+ * the library (8 MiB, held by every GPU that loads the library until the
+ * process exits).  n_sol * n_tets above MOREA_NOALLOC_MAX_TET_EVALS returns
+ * MOREA_EINVAL before anything is launched.  All calls on a device share
+ * that array: calls whose work overlaps on the GPU (on unordered streams)
+ * race and give wrong results; calls on one stream are safe.  The first call
+ * on each device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.
+ * Nothing is allocated and no memory of the caller is kept. */
+morea_status morea_fold_magnitude_noalloc(int32_t n_sol, int32_t n_points, int32_t n_tets,
+                                          const int32_t *tets, const float *ref_points,
+                                          const float *cdelta, int32_t nx, int32_t ny, int32_t nz,
+                                          int32_t subvoxel_bits, const float *src_pts,
+                                          const float *tgt_pts, double *f_mag, uint8_t *folded,
+                                          double *severity, void *stream);
+
 /* Static description of a status code. */
 const char *morea_status_string(morea_status s);
 

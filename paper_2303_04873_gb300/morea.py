@@ -36,8 +36,9 @@ ENTRY_POINTS = (
     "morea_create_problem", "morea_destroy_problem", "morea_eval_full", "morea_eval_partial",
     "morea_commit_partial", "morea_check_folds", "morea_read_records", "morea_read_totals",
     "morea_device_status", "morea_problem_info", "morea_profile", "morea_profile_read",
-    "morea_status_string",
+    "morea_fold_magnitude_noalloc", "morea_status_string",
 )
+NOALLOC_MAX_TET_EVALS = 524288
 
 TET_RECORD_DTYPE = np.dtype([
     ("e_img", "<f4", (2,)), ("e_guid", "<f4", (2,)), ("n_vox", "<i4", (2,)), ("n_gp", "<i4", (2,)),
@@ -95,6 +96,8 @@ def lib():
     L.morea_profile.argtypes = [vp, ctypes.c_uint32]
     L.morea_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                                      ctypes.POINTER(ctypes.c_int64)]
+    L.morea_fold_magnitude_noalloc.argtypes = [i32, i32, i32, vp, vp, vp, i32, i32, i32, i32, vp, vp, vp, u8p,
+                                               vp, vp]
     L.morea_status_string.argtypes = [i32]
     L.morea_status_string.restype = ctypes.c_char_p
     for name in ENTRY_POINTS:
@@ -317,6 +320,30 @@ class Problem:
         _check(self._L.morea_profile_read(self._h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(v)),
                "morea_profile_read")
         return ms.value, n.value, v.value
+
+
+def fold_magnitude_noalloc(tets: torch.Tensor, ref_points: torch.Tensor, cdelta: torch.Tensor, shape_xyz,
+                           subvoxel_bits: int, src: torch.Tensor, tgt: torch.Tensor, out=None, stream=None):
+    """Fold constraint and f_magnitude without a problem handle and without
+    any allocation inside the library (for callers that cannot allocate
+    device memory; see morea_fold_magnitude_noalloc in include/morea.h).
+    ``out`` = (f_mag [n] f64, folded [n] u8, severity [n] f64), preallocated
+    by the caller; when omitted this wrapper allocates them with torch."""
+    n, V = int(src.shape[0]), int(src.shape[1])
+    T = int(tets.shape[0])
+    if out is None:
+        out = (torch.empty(n, dtype=torch.float64, device=src.device),
+               torch.empty(n, dtype=torch.uint8, device=src.device),
+               torch.empty(n, dtype=torch.float64, device=src.device))
+    f_mag, folded, sev = out
+    nx, ny, nz = shape_xyz
+    _check(lib().morea_fold_magnitude_noalloc(
+        n, V, T, _dev(tets, torch.int32, (T, 4), "tets"), _dev(ref_points, torch.float32, (V, 3), "ref_points"),
+        _dev(cdelta, torch.float32, (T,), "cdelta"), int(nx), int(ny), int(nz), int(subvoxel_bits),
+        _dev(src, torch.float32, (n, V, 3), "src"), _dev(tgt, torch.float32, (n, V, 3), "tgt"),
+        _dev(f_mag, torch.float64, (n,), "f_mag"), _dev(folded, torch.uint8, (n,), "folded"),
+        _dev(sev, torch.float64, (n,), "severity"), _stream(stream)), "morea_fold_magnitude_noalloc")
+    return f_mag, folded, sev
 
 
 def requests_to_device(rd, device="cuda"):
