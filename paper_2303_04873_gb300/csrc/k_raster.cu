@@ -12,6 +12,12 @@
 // bit folded into B).  Each face bound is first estimated in FP32 and then
 // corrected with exact int64 evaluations, so the interval does not depend on
 // the estimate's rounding.
+//
+// Memory traffic per voxel visit: the own voxel (one 4- or 2-byte load), one
+// 16- or 8-byte load per z-plane of the other image's 2x2x2 neighbourhood
+// from its "quad" copy, and the band mask only in rows that touch a guidance
+// band.  Rows are distributed to lanes by a warp scan; each lane finds the
+// row of its voxel by a 5-step shuffle search.
 #include "morea_device.cuh"
 
 namespace morea {
@@ -21,24 +27,79 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 
 template <typename TI>
-__device__ __forceinline__ float ld_img(const TI *p, int idx);
-
+struct QuadOf;
 template <>
-__device__ __forceinline__ float ld_img<float>(const float *p, int idx)
+struct QuadOf<float> {
+    using T = float4;
+};
+template <>
+struct QuadOf<__half> {
+    using T = uint2;
+};
+
+__device__ __forceinline__ float ld_img(const float *p, int idx) { return __ldg(p + idx); }
+__device__ __forceinline__ float ld_img(const __half *p, int idx) { return __half2float(__ldg(p + idx)); }
+
+// one z-plane of the neighbourhood: (x,y), (x+1,y), (x,y+1), (x+1,y+1)
+__device__ __forceinline__ void ld_quad(const float4 *q, int idx, float &a, float &b, float &c, float &d)
 {
-    return __ldg(p + idx);
+    const float4 v = __ldg(q + idx);
+    a = v.x;
+    b = v.y;
+    c = v.z;
+    d = v.w;
 }
 
-template <>
-__device__ __forceinline__ float ld_img<__half>(const __half *p, int idx)
+__device__ __forceinline__ void ld_quad(const uint2 *q, int idx, float &a, float &b, float &c, float &d)
 {
-    return __half2float(__ldg(p + idx));
+    const uint2 v = __ldg(q + idx);
+    const float2 lo = __half22float2(*reinterpret_cast<const __half2 *>(&v.x));
+    const float2 hi = __half22float2(*reinterpret_cast<const __half2 *>(&v.y));
+    a = lo.x;
+    b = lo.y;
+    c = hi.x;
+    d = hi.y;
 }
 
 // Trilinear sample with the position clamped to [0, n-1] per axis and the
-// cell i0 = min(floor(y), n - 2).
-template <typename TI>
-__device__ __forceinline__ float trilin(const TI *img, int nx, int ny, int nz, float yx, float yy, float yz)
+// cell i0 = min(floor(y), n - 2), from the quad copy of the image.
+template <typename QT>
+__device__ __forceinline__ float trilin_quad(const QT *q, int nx, int ny, int nz, float yx, float yy, float yz)
+{
+    const float cx = fminf(fmaxf(yx, 0.0f), (float)(nx - 1));
+    const float cy = fminf(fmaxf(yy, 0.0f), (float)(ny - 1));
+    const float cz = fminf(fmaxf(yz, 0.0f), (float)(nz - 1));
+    const int ix = min((int)cx, nx - 2), iy = min((int)cy, ny - 2), iz = min((int)cz, nz - 2);
+    const float fx = cx - (float)ix, fy = cy - (float)iy, fz = cz - (float)iz;
+    const int b = (iz * ny + iy) * nx + ix;
+    float v000, v100, v010, v110, v001, v101, v011, v111;
+    ld_quad(q, b, v000, v100, v010, v110);
+    ld_quad(q, b + nx * ny, v001, v101, v011, v111);
+    const float c00 = fmaf(fx, v100 - v000, v000), c10 = fmaf(fx, v110 - v010, v010);
+    const float c01 = fmaf(fx, v101 - v001, v001), c11 = fmaf(fx, v111 - v011, v011);
+    const float c0 = fmaf(fy, c10 - c00, c00), c1 = fmaf(fy, c11 - c01, c01);
+    return fmaf(fz, c1 - c0, c0);
+}
+
+// The same sample when the position is known to lie strictly inside
+// [0, n-1] per axis: the clamps and the last-cell guard are no-ops there.
+template <typename QT>
+__device__ __forceinline__ float trilin_quad_inner(const QT *q, int nx, int ny, float yx, float yy, float yz)
+{
+    const int ix = (int)yx, iy = (int)yy, iz = (int)yz;
+    const float fx = yx - (float)ix, fy = yy - (float)iy, fz = yz - (float)iz;
+    const int b = (iz * ny + iy) * nx + ix;
+    float v000, v100, v010, v110, v001, v101, v011, v111;
+    ld_quad(q, b, v000, v100, v010, v110);
+    ld_quad(q, b + nx * ny, v001, v101, v011, v111);
+    const float c00 = fmaf(fx, v100 - v000, v000), c10 = fmaf(fx, v110 - v010, v010);
+    const float c01 = fmaf(fx, v101 - v001, v001), c11 = fmaf(fx, v111 - v011, v011);
+    const float c0 = fmaf(fy, c10 - c00, c00), c1 = fmaf(fy, c11 - c01, c01);
+    return fmaf(fz, c1 - c0, c0);
+}
+
+// The same sample from a plain FP32 image (guidance distance maps).
+__device__ __forceinline__ float trilin_plain(const float *img, int nx, int ny, int nz, float yx, float yy, float yz)
 {
     const float cx = fminf(fmaxf(yx, 0.0f), (float)(nx - 1));
     const float cy = fminf(fmaxf(yy, 0.0f), (float)(ny - 1));
@@ -47,10 +108,10 @@ __device__ __forceinline__ float trilin(const TI *img, int nx, int ny, int nz, f
     const float fx = cx - (float)ix, fy = cy - (float)iy, fz = cz - (float)iz;
     const int sy = nx, sz = nx * ny;
     const int b = (iz * ny + iy) * nx + ix;
-    const float v000 = ld_img(img, b), v100 = ld_img(img, b + 1);
-    const float v010 = ld_img(img, b + sy), v110 = ld_img(img, b + sy + 1);
-    const float v001 = ld_img(img, b + sz), v101 = ld_img(img, b + sz + 1);
-    const float v011 = ld_img(img, b + sz + sy), v111 = ld_img(img, b + sz + sy + 1);
+    const float v000 = __ldg(img + b), v100 = __ldg(img + b + 1);
+    const float v010 = __ldg(img + b + sy), v110 = __ldg(img + b + sy + 1);
+    const float v001 = __ldg(img + b + sz), v101 = __ldg(img + b + sz + 1);
+    const float v011 = __ldg(img + b + sz + sy), v111 = __ldg(img + b + sz + sy + 1);
     const float c00 = fmaf(fx, v100 - v000, v000), c10 = fmaf(fx, v110 - v010, v010);
     const float c01 = fmaf(fx, v101 - v001, v001), c11 = fmaf(fx, v111 - v011, v011);
     const float c0 = fmaf(fy, c10 - c00, c00), c1 = fmaf(fy, c11 - c01, c01);
@@ -115,13 +176,129 @@ __device__ __forceinline__ int face_hi(long long A, long long B, float est, int 
     return i;
 }
 
-template <typename TI, int HMODE, int GMODE>
-__global__ void __launch_bounds__(kBlock) k_raster(const DevProblem *__restrict__ probs,
-                                                  const WorkEntry *__restrict__ entries,
-                                                  const RasterSetup *__restrict__ setup,
-                                                  RasterOut *__restrict__ rout, const int *n_entries_dev,
-                                                  int n_entries_host)
+// Exact x-interval [lo, hi] of the voxel centres of row (jlo + dj, klo + dk).
+// Per face the FP32 root estimate decides whenever it is farther than the
+// face's error bound from the bounding-box ends and from every integer;
+// otherwise the bound is solved exactly in int64.
+__device__ __forceinline__ void row_interval(const FaceRow *__restrict__ f, int dj, int dk, int ilo, int ihi,
+                                             int &lo, int &hi)
 {
+    lo = ilo;
+    hi = ihi;
+    const float fdj = (float)dj, fdk = (float)dk;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float4 es = __ldg(reinterpret_cast<const float4 *>(&f[q].e0));       // e0, ey, ez, tol
+        const longlong2 ab = __ldg(reinterpret_cast<const longlong2 *>(&f[q].ax));  // ax, b00
+        const float est = fmaf(es.y, fdj, fmaf(es.z, fdk, es.x));
+        const float tol = es.w;
+        const float fl = floorf(est);
+        const float fr = est - fl;
+        if (ab.x > 0) {                       // inside for i > root: lo = floor(root) + 1
+            if (est + tol < (float)ilo) continue;
+            if (est - tol >= (float)ihi) { hi = lo - 1; continue; }
+            if (fr > tol && fr < 1.0f - tol) { lo = max(lo, (int)fl + 1); continue; }
+            const longlong2 yz = __ldg(reinterpret_cast<const longlong2 *>(&f[q].by));
+            lo = max(lo, face_lo(ab.x, ab.y + yz.x * dj + yz.y * dk, est, ilo, ihi));
+        } else if (ab.x < 0) {                // inside for i < root: hi = ceil(root) - 1
+            if (est - tol > (float)ihi) continue;
+            if (est + tol <= (float)ilo) { hi = lo - 1; continue; }
+            if (fr > tol && fr < 1.0f - tol) { hi = min(hi, (int)fl); continue; }
+            const longlong2 yz = __ldg(reinterpret_cast<const longlong2 *>(&f[q].by));
+            hi = min(hi, face_hi(ab.x, ab.y + yz.x * dj + yz.y * dk, est, ilo, ihi));
+        } else {                              // face parallel to x: the whole row or nothing
+            const longlong2 yz = __ldg(reinterpret_cast<const longlong2 *>(&f[q].by));
+            if (ab.y + yz.x * dj + yz.y * dk <= 0) hi = lo - 1;
+        }
+    }
+}
+
+// Continuous guidance term of one voxel that lies in at least one band.
+__device__ __forceinline__ void guidance_voxel(const DevProblem &P, int side, int idx, float yx, float yy, float yz,
+                                            float &s_g, float &c_g)
+{
+    const int nx = P.nx, ny = P.ny, nz = P.nz;
+    unsigned mk = P.band[side][idx];
+    while (mk) {
+        const int g = __ffs(mk) - 1;
+        mk &= mk - 1;
+        const size_t off = (size_t)g * ((size_t)nx * ny * nz);
+        const float av = __ldg(P.dmap[side] + off + idx);
+        if (av < P.r) {
+            const float dv = trilin_plain(P.dmap[1 - side] + off, nx, ny, nz, yx, yy, yz);
+            const float w = P.wgt[g] * (P.r - av) * P.inv_r;
+            const float df = av - dv;
+            kadd(s_g, c_g, w * df * df);
+        }
+    }
+}
+
+// Pair-transfer guidance of one tet copy: the guidance points of this side
+// located in the copy (exact perturbed inside test on their snapped
+// coordinates), mapped and compared with their partners.
+__device__ __forceinline__ void guidance_pairs(const DevProblem &P, const RasterSetup *su, int side, int lane,
+                                            float &s_g, float &c_g, int &ngp)
+{
+    const int cs = P.cshift, kb = P.kbits;
+    const int cx0 = max(0, su->qlo[0] >> cs), cx1 = min(P.cgx - 1, su->qhi[0] >> cs);
+    const int cy0 = max(0, su->qlo[1] >> cs), cy1 = min(P.cgy - 1, su->qhi[1] >> cs);
+    const int cz0 = max(0, su->qlo[2] >> cs), cz1 = min(P.cgz - 1, su->qhi[2] >> cs);
+    const float inv_s = 1.0f / (float)P.S;
+    const float *M = su->M;
+    for (int cz = cz0; cz <= cz1; ++cz)
+        for (int cy = cy0; cy <= cy1; ++cy)
+            for (int cx = cx0; cx <= cx1; ++cx) {
+                const int c = (cz * P.cgy + cy) * P.cgx + cx;
+                const int p0 = P.cell_start[side][c], p1 = P.cell_start[side][c + 1];
+                for (int p = p0 + lane; p < p1; p += 32) {
+                    const int mi = P.cell_pts[side][p];
+                    const int4 q = P.gq[side][mi];
+                    bool in = true;
+#pragma unroll
+                    for (int f = 0; f < 4; ++f) {
+                        const long long val = (su->f[f].ax >> kb) * q.x + (su->f[f].by >> kb) * q.y +
+                                              (su->f[f].bz >> kb) * q.z + su->ct[f];
+                        in = in && val > 0;
+                    }
+                    if (in) {
+                        const float dx = q.x * inv_s - 0.5f - su->s0[0];
+                        const float dy = q.y * inv_s - 0.5f - su->s0[1];
+                        const float dz = q.z * inv_s - 0.5f - su->s0[2];
+                        const float4 go = P.gp[1 - side][mi];
+                        const float ex = fmaf(M[0], dx, fmaf(M[1], dy, fmaf(M[2], dz, su->t0[0]))) - go.x;
+                        const float ey = fmaf(M[3], dx, fmaf(M[4], dy, fmaf(M[5], dz, su->t0[1]))) - go.y;
+                        const float ez = fmaf(M[6], dx, fmaf(M[7], dy, fmaf(M[8], dz, su->t0[2]))) - go.z;
+                        kadd(s_g, c_g, fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
+                        ngp += 1;
+                    }
+                }
+            }
+}
+
+// Pass modes of the image kernel.
+constexpr int kPassImage = 0;       // f_intensity only
+constexpr int kPassImageBand = 1;   // f_intensity + record the rows that touch a guidance band
+constexpr int kPassImagePairs = 2;  // f_intensity + pair-transfer guidance
+
+// Band-row records: per (entry, side) up to kBandRows segments (x range,
+// row) of voxels that may lie in a guidance band; k_guidance processes them.
+// A count above kBandRows means "overflow: recompute the rows".
+constexpr int kBandRows = kBandRowsPerItem;
+
+__device__ __forceinline__ int2 pack_band_row(int lo, int hi, int j, int k)
+{
+    return make_int2(lo | (hi << 16), j | (k << 16));
+}
+
+// Image pass (a4, a5, a7): one warp per (entry, side).
+template <typename TI, int HMODE, int PASS>
+__global__ void __launch_bounds__(kBlock, 4) k_raster(const DevProblem *__restrict__ probs,
+                                                     const WorkEntry *__restrict__ entries,
+                                                     const RasterSetup *__restrict__ setup,
+                                                     RasterOut *__restrict__ rout, int2 *__restrict__ bandrows,
+                                                     const int *n_entries_dev, int n_entries_host)
+{
+    using QT = typename QuadOf<TI>::T;
     const int lane = threadIdx.x & 31;
     const int n_ent = n_entries_dev ? min(*n_entries_dev, n_entries_host) : n_entries_host;
     const int n_items = 2 * n_ent;
@@ -131,45 +308,56 @@ __global__ void __launch_bounds__(kBlock) k_raster(const DevProblem *__restrict_
         const int side = item >= n_ent ? 1 : 0;      // all source sides first, then all target sides
         const int e = item - side * n_ent;
         const RasterSetup *su = setup + 2 * (size_t)e + side;
+        const unsigned char *sb = reinterpret_cast<const unsigned char *>(su);
+        const float4 m0 = __ldg(reinterpret_cast<const float4 *>(sb + offsetof(RasterSetup, M)));
+        const float4 m1 = __ldg(reinterpret_cast<const float4 *>(sb + offsetof(RasterSetup, M) + 16));
+        const float4 m2 = __ldg(reinterpret_cast<const float4 *>(sb + offsetof(RasterSetup, M) + 32));
+        const float4 t4 = __ldg(reinterpret_cast<const float4 *>(sb + offsetof(RasterSetup, t0)));
+        const int4 bx = __ldg(reinterpret_cast<const int4 *>(sb + offsetof(RasterSetup, ilo)));
+        const int2 bz2 = __ldg(reinterpret_cast<const int2 *>(sb + offsetof(RasterSetup, klo)));
+        const int valid = __float_as_int(t4.w);
+        // M = (m0.x m0.y m0.z; m0.w m1.x m1.y; m1.z m1.w m2.x), s0 = m2.yzw, t0 = t4.xyz
         float s_img = 0.0f, c_img = 0.0f, s_g = 0.0f, c_g = 0.0f;
         int nvox = 0, ngp = 0;
-        if (su->valid) {
+        int nband = 0;                                // band rows recorded (warp-uniform)
+        int2 *brec = PASS == kPassImageBand ? bandrows + (2 * (size_t)e + side) * kBandRows : nullptr;
+        if (valid & 1) {
             const DevProblem &P = probs[entries[e].prob];
             const int nx = P.nx, ny = P.ny, nz = P.nz;
             const TI *own = (const TI *)P.img[side];
-            const TI *oth = (const TI *)P.img[1 - side];
-            const int ilo = su->ilo, ihi = su->ihi, jlo = su->jlo, klo = su->klo;
-            const int nyb = su->jhi - jlo + 1, nzb = su->khi - klo + 1;
-            const int n_rows = (ilo <= ihi && nyb > 0 && nzb > 0) ? nyb * nzb : 0;
-            const float M0 = su->M[0], M1 = su->M[1], M2 = su->M[2];
-            const float M3 = su->M[3], M4 = su->M[4], M5 = su->M[5];
-            const float M6 = su->M[6], M7 = su->M[7], M8 = su->M[8];
-            const float s0x = su->s0[0], s0y = su->s0[1], s0z = su->s0[2];
-            const float t0x = su->t0[0], t0y = su->t0[1], t0z = su->t0[2];
+            const QT *oq = (const QT *)P.quad[1 - side];
+            const int ilo = bx.x, ihi = bx.y, jlo = bx.z, klo = bz2.x;
+            const int nyb = max(bx.w - jlo + 1, 1), nzb = bz2.y - klo + 1;
+            const int n_rows = (ilo <= ihi && bx.w >= jlo && nzb > 0) ? nyb * nzb : 0;
+            const bool inner = (valid & 2) != 0;
+            // lane -> row (jlo + dj, klo + dk); rows advance by 32 per batch
+            int dk = lane / nyb, dj = lane - dk * nyb;
+            const int inc_k = 32 / nyb, inc_j = 32 - inc_k * nyb;
             for (int rb = 0; rb < n_rows; rb += 32) {
-                const int r = rb + lane;
-                int lo = 1, hi = 0, j = 0, k = 0;
-                if (r < n_rows) {
-                    const int dk = r / nyb, dj = r - dk * nyb;
-                    j = jlo + dj;
-                    k = klo + dk;
-                    lo = ilo;
-                    hi = ihi;
-#pragma unroll
-                    for (int f = 0; f < 4; ++f) {
-                        const long long A = su->ax[f];
-                        const long long B = su->b00[f] + su->by[f] * dj + su->bz[f] * dk;
-                        if (A > 0) {
-                            const float est = fmaf(su->ey[f], (float)dj, fmaf(su->ez[f], (float)dk, su->e0[f]));
-                            lo = max(lo, face_lo(A, B, est, ilo, ihi));
-                        } else if (A < 0) {
-                            const float est = fmaf(su->ey[f], (float)dj, fmaf(su->ez[f], (float)dk, su->e0[f]));
-                            hi = min(hi, face_hi(A, B, est, ilo, ihi));
-                        } else if (B <= 0) {
-                            lo = 1;
-                            hi = 0;
-                        }
+                int lo = 1, hi = 0;
+                const int j = jlo + dj, k = klo + dk;
+                if (dk < nzb) row_interval(su->f, dj, dk, ilo, ihi, lo, hi);
+                if (PASS == kPassImageBand) {
+                    // record the band part of each row (warp-aggregated append)
+                    int blo = 1, bhi = 0;
+                    if (dk < nzb && hi >= lo) {
+                        const short2 br = __ldg(P.bandrow[side] + (k * ny + j));
+                        blo = max(lo, (int)br.x);
+                        bhi = min(hi, (int)br.y);
                     }
+                    const bool band = blo <= bhi;
+                    const unsigned bm = __ballot_sync(FULL, band);
+                    if (bm) {
+                        const int pos = nband + __popc(bm & ((1u << lane) - 1u));
+                        if (band && pos < kBandRows) brec[pos] = pack_band_row(blo, bhi, j, k);
+                        nband += __popc(bm);
+                    }
+                }
+                dj += inc_j;
+                dk += inc_k;
+                if (dj >= nyb) {
+                    dj -= nyb;
+                    dk += 1;
                 }
                 const int cnt = max(0, hi - lo + 1);
                 int incl = cnt;
@@ -180,90 +368,43 @@ __global__ void __launch_bounds__(kBlock) k_raster(const DevProblem *__restrict_
                 }
                 const int total = __shfl_sync(FULL, incl, 31);
                 nvox += total;
-                const int excl = incl - cnt;
+                const int d = lo - (incl - cnt);          // x = d + v for the row's voxels
+                const int jk = j | (k << 16);
                 for (int vb = 0; vb < total; vb += 32) {
                     const int v = vb + lane;
-                    int own_l = 0;
+                    int ow = 0;
 #pragma unroll
                     for (int step = 16; step >= 1; step >>= 1) {
-                        const int p = __shfl_sync(FULL, incl, own_l + step - 1);
-                        if (p <= v) own_l += step;
+                        const int p = __shfl_sync(FULL, incl, ow + step - 1);
+                        if (p <= v) ow += step;
                     }
-                    const int ox = __shfl_sync(FULL, lo, own_l);
-                    const int oe = __shfl_sync(FULL, excl, own_l);
-                    const int oj = __shfl_sync(FULL, j, own_l);
-                    const int ok = __shfl_sync(FULL, k, own_l);
+                    const int od = __shfl_sync(FULL, d, ow);
+                    const int ojk = __shfl_sync(FULL, jk, ow);
                     if (v < total) {
-                        const int x = ox + (v - oe);
-                        const int idx = (ok * ny + oj) * nx + x;
+                        const int x = od + v;
+                        const int oj = ojk & 0xffff, okk = ojk >> 16;
+                        const int idx = (okk * ny + oj) * nx + x;
                         const float a = ld_img(own, idx);
-                        const float dx = (float)x - s0x, dy = (float)oj - s0y, dz = (float)ok - s0z;
-                        const float yx = fmaf(M0, dx, fmaf(M1, dy, fmaf(M2, dz, t0x)));
-                        const float yy = fmaf(M3, dx, fmaf(M4, dy, fmaf(M5, dz, t0y)));
-                        const float yz = fmaf(M6, dx, fmaf(M7, dy, fmaf(M8, dz, t0z)));
-                        const float b = trilin(oth, nx, ny, nz, yx, yy, yz);
+                        const float dx = (float)x - m2.y, dy = (float)oj - m2.z, dz = (float)okk - m2.w;
+                        const float yx = fmaf(m0.x, dx, fmaf(m0.y, dy, fmaf(m0.z, dz, t4.x)));
+                        const float yy = fmaf(m0.w, dx, fmaf(m1.x, dy, fmaf(m1.y, dz, t4.y)));
+                        const float yz = fmaf(m1.z, dx, fmaf(m1.w, dy, fmaf(m2.x, dz, t4.z)));
+                        const float b = inner ? trilin_quad_inner(oq, nx, ny, yx, yy, yz)
+                                              : trilin_quad(oq, nx, ny, nz, yx, yy, yz);
                         kadd(s_img, c_img, hfun<HMODE>(a, b));
-                        if (GMODE == MOREA_G_CONTINUOUS) {
-                            unsigned mk = P.band[side][idx];
-                            while (mk) {
-                                const int g = __ffs(mk) - 1;
-                                mk &= mk - 1;
-                                const size_t off = (size_t)g * ((size_t)nx * ny * nz);
-                                const float av = __ldg(P.dmap[side] + off + idx);
-                                if (av < P.r) {
-                                    const float dv = trilin(P.dmap[1 - side] + off, nx, ny, nz, yx, yy, yz);
-                                    const float w = P.wgt[g] * (P.r - av) * P.inv_r;
-                                    const float df = av - dv;
-                                    kadd(s_g, c_g, w * df * df);
-                                }
-                            }
-                        }
                     }
                 }
             }
-            if (GMODE == MOREA_G_PAIR_TRANSFER && P.n_guid > 0) {
-                // guidance points of this side located in the copy (exact
-                // perturbed inside test on their snapped coordinates)
-                const int cs = P.cshift;
-                const int cx0 = max(0, su->qlo[0] >> cs), cx1 = min(P.cgx - 1, su->qhi[0] >> cs);
-                const int cy0 = max(0, su->qlo[1] >> cs), cy1 = min(P.cgy - 1, su->qhi[1] >> cs);
-                const int cz0 = max(0, su->qlo[2] >> cs), cz1 = min(P.cgz - 1, su->qhi[2] >> cs);
-                const int kb = P.kbits;
-                const float inv_s = 1.0f / (float)P.S;
-                for (int cz = cz0; cz <= cz1; ++cz)
-                    for (int cy = cy0; cy <= cy1; ++cy)
-                        for (int cx = cx0; cx <= cx1; ++cx) {
-                            const int c = (cz * P.cgy + cy) * P.cgx + cx;
-                            const int p0 = P.cell_start[side][c], p1 = P.cell_start[side][c + 1];
-                            for (int p = p0 + lane; p < p1; p += 32) {
-                                const int mi = P.cell_pts[side][p];
-                                const int4 q = P.gq[side][mi];
-                                bool in = true;
-#pragma unroll
-                                for (int f = 0; f < 4; ++f) {
-                                    const long long val = (su->ax[f] >> kb) * q.x + (su->by[f] >> kb) * q.y +
-                                                          (su->bz[f] >> kb) * q.z + su->ct[f];
-                                    in = in && val > 0;
-                                }
-                                if (in) {
-                                    const float dx = q.x * inv_s - 0.5f - s0x;
-                                    const float dy = q.y * inv_s - 0.5f - s0y;
-                                    const float dz = q.z * inv_s - 0.5f - s0z;
-                                    const float4 go = P.gp[1 - side][mi];
-                                    const float ex = fmaf(M0, dx, fmaf(M1, dy, fmaf(M2, dz, t0x))) - go.x;
-                                    const float ey = fmaf(M3, dx, fmaf(M4, dy, fmaf(M5, dz, t0y))) - go.y;
-                                    const float ez = fmaf(M6, dx, fmaf(M7, dy, fmaf(M8, dz, t0z))) - go.z;
-                                    kadd(s_g, c_g, fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
-                                    ngp += 1;
-                                }
-                            }
-                        }
-            }
+            if (PASS == kPassImagePairs && P.n_guid > 0) guidance_pairs(P, su, side, lane, s_g, c_g, ngp);
         }
         const float e_img = warp_comp_sum(s_img, -c_img);
-        const float e_g = warp_comp_sum(s_g, -c_g);
+        float e_g = 0.0f;
+        if (PASS == kPassImagePairs) {
+            e_g = warp_comp_sum(s_g, -c_g);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) ngp += __shfl_xor_sync(FULL, ngp, o);
+            for (int o = 16; o > 0; o >>= 1) ngp += __shfl_xor_sync(FULL, ngp, o);
+        }
+        if (PASS == kPassImageBand) ngp = nband;      // band rows for k_guidance (cleared there)
         if (lane == 0) {
             RasterOut ro;
             ro.e_img = e_img;
@@ -275,20 +416,151 @@ __global__ void __launch_bounds__(kBlock) k_raster(const DevProblem *__restrict_
     }
 }
 
+// Continuous guidance (a6): for every (entry, side) with band rows, the band
+// voxels of those rows (rows recorded by the image pass, or recomputed when
+// there were more than kBandRows; band voxels from the per-row sorted
+// list); writes e_guid and clears the count.  Mapped positions use the same
+// FP32 affine map as the image pass.
+__global__ void __launch_bounds__(kBlock, 4) k_guidance(const DevProblem *__restrict__ probs,
+                                                       const WorkEntry *__restrict__ entries,
+                                                       const RasterSetup *__restrict__ setup,
+                                                       RasterOut *__restrict__ rout,
+                                                       const int2 *__restrict__ bandrows, const int *n_entries_dev,
+                                                       int n_entries_host)
+{
+    const int lane = threadIdx.x & 31;
+    const int n_ent = n_entries_dev ? min(*n_entries_dev, n_entries_host) : n_entries_host;
+    const int n_items = 2 * n_ent;
+    const int wpb = blockDim.x >> 5;
+    const int nwarps = gridDim.x * wpb;
+    for (int item = blockIdx.x * wpb + (threadIdx.x >> 5); item < n_items; item += nwarps) {
+        const int side = item >= n_ent ? 1 : 0;
+        const int e = item - side * n_ent;
+        RasterOut *ro = rout + 2 * (size_t)e + side;
+        const int nband = ro->n_gp;                   // warp-uniform
+        if (nband == 0) continue;
+        const RasterSetup *su = setup + 2 * (size_t)e + side;
+        const unsigned char *sb = reinterpret_cast<const unsigned char *>(su);
+        const float4 m0 = __ldg(reinterpret_cast<const float4 *>(sb + offsetof(RasterSetup, M)));
+        const float4 m1 = __ldg(reinterpret_cast<const float4 *>(sb + offsetof(RasterSetup, M) + 16));
+        const float4 m2 = __ldg(reinterpret_cast<const float4 *>(sb + offsetof(RasterSetup, M) + 32));
+        const float4 t4 = __ldg(reinterpret_cast<const float4 *>(sb + offsetof(RasterSetup, t0)));
+        const int4 bx = __ldg(reinterpret_cast<const int4 *>(sb + offsetof(RasterSetup, ilo)));
+        const int2 bz2 = __ldg(reinterpret_cast<const int2 *>(sb + offsetof(RasterSetup, klo)));
+        const DevProblem &P = probs[entries[e].prob];
+        const int nx = P.nx, ny = P.ny;
+        const int2 *brec = bandrows + (2 * (size_t)e + side) * kBandRows;
+        const bool recorded = nband <= kBandRows;
+        const int ilo = bx.x, ihi = bx.y, jlo = bx.z, klo = bz2.x;
+        const int nyb = max(bx.w - jlo + 1, 1), nzb = bz2.y - klo + 1;
+        const int n_rows = recorded ? nband : ((ilo <= ihi && bx.w >= jlo && nzb > 0) ? nyb * nzb : 0);
+        float s_g = 0.0f, c_g = 0.0f;
+        int dk = lane / nyb, dj = lane - dk * nyb;
+        const int inc_k = 32 / nyb, inc_j = 32 - inc_k * nyb;
+        for (int rb = 0; rb < n_rows; rb += 32) {
+            int lo = 1, hi = 0, j = 0, k = 0;   // x range of the row part, then band-list positions
+            if (recorded) {
+                if (rb + lane < n_rows) {
+                    const int2 rec = brec[rb + lane];
+                    lo = rec.x & 0xffff;
+                    hi = rec.x >> 16;
+                    j = rec.y & 0xffff;
+                    k = rec.y >> 16;
+                }
+            } else {
+                j = jlo + dj;
+                k = klo + dk;
+                if (dk < nzb) {
+                    row_interval(su->f, dj, dk, ilo, ihi, lo, hi);
+                    if (hi >= lo) {
+                        const short2 br = __ldg(P.bandrow[side] + (k * ny + j));
+                        lo = max(lo, (int)br.x);
+                        hi = min(hi, (int)br.y);
+                    }
+                }
+                dj += inc_j;
+                dk += inc_k;
+                if (dj >= nyb) {
+                    dj -= nyb;
+                    dk += 1;
+                }
+            }
+            // the band voxels of row (j, k) with lo <= x <= hi: positions [a, b) of the row's list
+            int a = 0, cnt = 0;
+            if (hi >= lo) {
+                const int row = k * ny + j;
+                int b0 = P.band_start[side][row], b1 = P.band_start[side][row + 1];
+                const short *bx_ = P.band_x[side];
+                int l = b0, r = b1;                   // first position with x >= lo
+                while (l < r) {
+                    const int m = (l + r) >> 1;
+                    if (bx_[m] < lo) l = m + 1; else r = m;
+                }
+                a = l;
+                r = b1;                               // first position with x > hi
+                while (l < r) {
+                    const int m = (l + r) >> 1;
+                    if (bx_[m] <= hi) l = m + 1; else r = m;
+                }
+                cnt = l - a;
+            }
+            int incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const int total = __shfl_sync(FULL, incl, 31);
+            const int d = a - (incl - cnt);           // list position = d + v
+            const int jk = j | (k << 16);
+            for (int vb = 0; vb < total; vb += 32) {
+                const int v = vb + lane;
+                int ow = 0;
+#pragma unroll
+                for (int step = 16; step >= 1; step >>= 1) {
+                    const int p = __shfl_sync(FULL, incl, ow + step - 1);
+                    if (p <= v) ow += step;
+                }
+                const int od = __shfl_sync(FULL, d, ow);
+                const int ojk = __shfl_sync(FULL, jk, ow);
+                if (v < total) {
+                    const int x = P.band_x[side][od + v];
+                    const int oj = ojk & 0xffff, okk = ojk >> 16;
+                    const int idx = (okk * ny + oj) * nx + x;
+                    const float dx = (float)x - m2.y, dy = (float)oj - m2.z, dz = (float)okk - m2.w;
+                    const float yx = fmaf(m0.x, dx, fmaf(m0.y, dy, fmaf(m0.z, dz, t4.x)));
+                    const float yy = fmaf(m0.w, dx, fmaf(m1.x, dy, fmaf(m1.y, dz, t4.y)));
+                    const float yz = fmaf(m1.z, dx, fmaf(m1.w, dy, fmaf(m2.x, dz, t4.z)));
+                    guidance_voxel(P, side, idx, yx, yy, yz, s_g, c_g);
+                }
+            }
+        }
+        const float e_g = warp_comp_sum(s_g, -c_g);
+        if (lane == 0) {
+            ro->e_guid = e_g;
+            ro->n_gp = 0;
+        }
+    }
+}
+
 template <typename TI, int HMODE>
 cudaError_t launch_g(const DevProblem *probs, int g_mode, const WorkEntry *entries, const RasterSetup *setup,
-                     RasterOut *rout, const int *n_dev, int n_host, int grid, cudaStream_t st)
+                     RasterOut *rout, int2 *bandrows, const int *n_dev, int n_host, int grid, cudaStream_t st)
 {
     switch (g_mode) {
     case MOREA_G_CONTINUOUS:
-        k_raster<TI, HMODE, MOREA_G_CONTINUOUS><<<grid, kBlock, 0, st>>>(probs, entries, setup, rout, n_dev, n_host);
+        k_raster<TI, HMODE, kPassImageBand><<<grid, kBlock, 0, st>>>(probs, entries, setup, rout, bandrows, n_dev,
+                                                                    n_host);
+        if (cudaPeekAtLastError() == cudaSuccess)
+            k_guidance<<<grid, kBlock, 0, st>>>(probs, entries, setup, rout, bandrows, n_dev, n_host);
         break;
     case MOREA_G_PAIR_TRANSFER:
-        k_raster<TI, HMODE, MOREA_G_PAIR_TRANSFER><<<grid, kBlock, 0, st>>>(probs, entries, setup, rout, n_dev,
-                                                                           n_host);
+        k_raster<TI, HMODE, kPassImagePairs><<<grid, kBlock, 0, st>>>(probs, entries, setup, rout, bandrows, n_dev,
+                                                                     n_host);
         break;
     default:
-        k_raster<TI, HMODE, MOREA_G_OFF><<<grid, kBlock, 0, st>>>(probs, entries, setup, rout, n_dev, n_host);
+        k_raster<TI, HMODE, kPassImage><<<grid, kBlock, 0, st>>>(probs, entries, setup, rout, bandrows, n_dev,
+                                                                n_host);
         break;
     }
     return cudaGetLastError();
@@ -297,21 +569,21 @@ cudaError_t launch_g(const DevProblem *probs, int g_mode, const WorkEntry *entri
 }  // namespace
 
 cudaError_t launch_raster(const DevProblem *probs, const DevProblem &hp, const WorkEntry *entries,
-                          const RasterSetup *setup, RasterOut *rout, const int *n_entries_dev,
+                          const RasterSetup *setup, RasterOut *rout, int2 *bandrows, const int *n_entries_dev,
                           int n_entries_host, int grid, cudaStream_t st)
 {
     if (grid <= 0) grid = sm_count() * 8;
     if (hp.dtype == MOREA_F16) {
         if (hp.h_mode == MOREA_H_MOREA_FG)
-            return launch_g<__half, MOREA_H_MOREA_FG>(probs, hp.g_mode, entries, setup, rout, n_entries_dev,
+            return launch_g<__half, MOREA_H_MOREA_FG>(probs, hp.g_mode, entries, setup, rout, bandrows, n_entries_dev,
                                                       n_entries_host, grid, st);
-        return launch_g<__half, MOREA_H_PLAIN_SSD>(probs, hp.g_mode, entries, setup, rout, n_entries_dev,
+        return launch_g<__half, MOREA_H_PLAIN_SSD>(probs, hp.g_mode, entries, setup, rout, bandrows, n_entries_dev,
                                                    n_entries_host, grid, st);
     }
     if (hp.h_mode == MOREA_H_MOREA_FG)
-        return launch_g<float, MOREA_H_MOREA_FG>(probs, hp.g_mode, entries, setup, rout, n_entries_dev,
+        return launch_g<float, MOREA_H_MOREA_FG>(probs, hp.g_mode, entries, setup, rout, bandrows, n_entries_dev,
                                                  n_entries_host, grid, st);
-    return launch_g<float, MOREA_H_PLAIN_SSD>(probs, hp.g_mode, entries, setup, rout, n_entries_dev,
+    return launch_g<float, MOREA_H_PLAIN_SSD>(probs, hp.g_mode, entries, setup, rout, bandrows, n_entries_dev,
                                               n_entries_host, grid, st);
 }
 

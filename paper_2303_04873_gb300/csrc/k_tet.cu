@@ -41,22 +41,38 @@ __global__ void __launch_bounds__(kBlock) k_snap_slots(const DevProblem *__restr
     }
 }
 
-__device__ __forceinline__ void build_entry_work(const DevProblem &P, const WorkEntry &we, int e,
-                                                 RasterSetup *setup, TetOut *tout)
+// Per-entry work of the tet pass: one thread per (entry, side) builds that
+// copy's rasterisation set-up; the side-0 thread also evaluates the fold and
+// magnitude terms of the tet.
+__global__ void __launch_bounds__(kBlock) k_entry_work(const DevProblem *__restrict__ probs,
+                                                      const WorkEntry *__restrict__ entries, RasterSetup *setup,
+                                                      TetOut *tout, const int *n_entries_dev, int n_entries_host)
 {
-    TetOut to;
-    tet_terms(we.q[0], we.q[1], P, we.tet, to);
-    tout[e] = to;
-    RasterSetup su;
-    make_setup(we.q[0], we.q[1], P, su);
-    setup[2 * (size_t)e] = su;
-    make_setup(we.q[1], we.q[0], P, su);
-    setup[2 * (size_t)e + 1] = su;
+    const int n_ent = n_entries_dev ? min(*n_entries_dev, n_entries_host) : n_entries_host;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < 2LL * n_ent;
+         g += (long long)gridDim.x * blockDim.x) {
+        const int e = (int)(g >> 1), side = (int)(g & 1);
+        const WorkEntry &we = entries[e];
+        const DevProblem &P = probs[we.prob];
+        int4 own[4], oth[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            own[m] = we.q[side][m];
+            oth[m] = we.q[1 - side][m];
+        }
+        RasterSetup su;
+        make_setup(own, oth, P, su);
+        setup[g] = su;
+        if (side == 0) {
+            TetOut to;
+            tet_terms(own, oth, P, we.tet, to);
+            tout[e] = to;
+        }
+    }
 }
 
 __global__ void __launch_bounds__(kBlock) k_full_entries(const DevProblem *__restrict__ dp, int n_sol,
-                                                        const int *__restrict__ slot, WorkEntry *entries,
-                                                        RasterSetup *setup, TetOut *tout)
+                                                        const int *__restrict__ slot, WorkEntry *entries)
 {
     const DevProblem &P = *dp;
     const int T = P.n_tets, V = P.n_points;
@@ -81,7 +97,6 @@ __global__ void __launch_bounds__(kBlock) k_full_entries(const DevProblem *__res
             we.q[1][m] = sq[V + vid[m]];
         }
         entries[e] = we;
-        build_entry_work(P, we, (int)e, setup, tout);
     }
 }
 
@@ -223,8 +238,8 @@ __global__ void __launch_bounds__(kBlock) k_partial_entries(
     const DevProblem *__restrict__ dp, int n_req, const int *__restrict__ slot,
     const int *__restrict__ chg_off, const int *__restrict__ chg_pts, const float *__restrict__ chg_src,
     const float *__restrict__ chg_tgt, int max_changed, const int *__restrict__ v2t_off,
-    const int *__restrict__ v2t_idx, WorkEntry *entries, RasterSetup *setup, TetOut *tout, int cap,
-    int *counter, ReqInfo *rinfo, int *req_chg_pts, int4 *req_chg_q)
+    const int *__restrict__ v2t_idx, WorkEntry *entries, int cap, int *counter, ReqInfo *rinfo,
+    int *req_chg_pts, int4 *req_chg_q)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_err, s_base, s_m, s_a, s_slot;
@@ -309,31 +324,33 @@ __global__ void __launch_bounds__(kBlock) k_partial_entries(
         }
         return;
     }
-    const int4 *sq = P.slot_q + (size_t)s * 2 * V;
+    // compaction: the owner of each bitmap word writes its tets' ids in order
     int pos = s_base + excl;
     for (int w = w0; w < w1; ++w) {
         unsigned b = bits[w];
         while (b) {
-            const int t = (w << 5) + __ffs(b) - 1;
+            entries[pos++].tet = (w << 5) + __ffs(b) - 1;
             b &= b - 1;
-            const int4 tv = P.tets[t];
-            const int vid[4] = {tv.x, tv.y, tv.z, tv.w};
-            WorkEntry we;
-            we.req = r;
-            we.slot = s;
-            we.tet = t;
-            we.prob = 0;
+        }
+    }
+    __syncthreads();
+    // all threads fill the entries: vertices from the request or the slot
+    const int4 *sq = P.slot_q + (size_t)s * 2 * V;
+    for (int k = tid; k < total; k += kBlock) {
+        WorkEntry &we = entries[s_base + k];
+        const int t = we.tet;
+        const int4 tv = P.tets[t];
+        const int vid[4] = {tv.x, tv.y, tv.z, tv.w};
+        we.req = r;
+        we.slot = s;
+        we.prob = 0;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                int hit = -1;
-                for (int c = 0; c < m; ++c)
-                    if (cid[c] == vid[k]) { hit = c; break; }
-                we.q[0][k] = hit >= 0 ? cq[2 * hit] : sq[vid[k]];
-                we.q[1][k] = hit >= 0 ? cq[2 * hit + 1] : sq[V + vid[k]];
-            }
-            entries[pos] = we;
-            build_entry_work(P, we, pos, setup, tout);
-            ++pos;
+        for (int q = 0; q < 4; ++q) {
+            int hit = -1;
+            for (int c = 0; c < m; ++c)
+                if (cid[c] == vid[q]) { hit = c; break; }
+            we.q[0][q] = hit >= 0 ? cq[2 * hit] : sq[vid[q]];
+            we.q[1][q] = hit >= 0 ? cq[2 * hit + 1] : sq[V + vid[q]];
         }
     }
     for (int c = tid; c < m; c += kBlock) {
@@ -544,6 +561,57 @@ __global__ void __launch_bounds__(kBlock) k_count_visits(const RasterOut *__rest
     if (threadIdx.x == 0 && c) atomicAdd(visits, c);
 }
 
+// The gather copy of an image: per voxel the four values (x, y), (x+1, y),
+// (x, y+1), (x+1, y+1) of its z-plane (indices clamped at the last row and
+// column, which the trilinear cell never uses), so one 16-byte (FP32) or
+// 8-byte (FP16) load brings one plane of the 2x2x2 neighbourhood.
+template <typename TI, typename QT>
+__global__ void __launch_bounds__(kBlock) k_build_quads(const TI *__restrict__ img, int nx, int ny, int nz, QT *quad);
+
+template <>
+__global__ void __launch_bounds__(kBlock) k_build_quads<float, float4>(const float *__restrict__ img, int nx, int ny,
+                                                                      int nz, float4 *quad)
+{
+    const long long N = (long long)nx * ny * nz;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < N;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(idx % nx), y = (int)((idx / nx) % ny);
+        const long long dx = x + 1 < nx ? 1 : 0, dy = y + 1 < ny ? nx : 0;
+        quad[idx] = make_float4(img[idx], img[idx + dx], img[idx + dy], img[idx + dx + dy]);
+    }
+}
+
+template <>
+__global__ void __launch_bounds__(kBlock) k_build_quads<unsigned short, uint2>(const unsigned short *__restrict__ img,
+                                                                              int nx, int ny, int nz, uint2 *quad)
+{
+    const long long N = (long long)nx * ny * nz;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < N;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(idx % nx), y = (int)((idx / nx) % ny);
+        const long long dx = x + 1 < nx ? 1 : 0, dy = y + 1 < ny ? nx : 0;
+        quad[idx] = make_uint2((unsigned)img[idx] | ((unsigned)img[idx + dx] << 16),
+                               (unsigned)img[idx + dy] | ((unsigned)img[idx + dx + dy] << 16));
+    }
+}
+
+// x-range of the voxels of each image row that lie in some guidance band.
+__global__ void __launch_bounds__(kBlock) k_band_rows(const uint8_t *__restrict__ band, int nx, int ny, int nz,
+                                                     short2 *bandrow)
+{
+    const int rows = ny * nz;
+    for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < rows; row += gridDim.x * blockDim.x) {
+        const uint8_t *b = band + (size_t)row * nx;
+        int lo = 32767, hi = -1;
+        for (int x = 0; x < nx; ++x)
+            if (b[x]) {
+                lo = min(lo, x);
+                hi = x;
+            }
+        bandrow[row] = make_short2((short)lo, (short)hi);
+    }
+}
+
 inline int grid_for(long long work, int block = kBlock)
 {
     long long b = (work + block - 1) / block;
@@ -578,8 +646,35 @@ cudaError_t launch_snap_slots(const DevProblem *dp, const DevProblem &hp, int n_
 cudaError_t launch_full_entries(const DevProblem *dp, const DevProblem &hp, int n_sol, const int *slot,
                                 WorkEntry *entries, RasterSetup *setup, TetOut *tout, cudaStream_t st)
 {
-    k_full_entries<<<grid_for((long long)n_sol * hp.n_tets), kBlock, 0, st>>>(dp, n_sol, slot, entries,
-                                                                             setup, tout);
+    k_full_entries<<<grid_for((long long)n_sol * hp.n_tets), kBlock, 0, st>>>(dp, n_sol, slot, entries);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_entry_work(dp, entries, setup, tout, nullptr, n_sol * hp.n_tets, st);
+}
+
+cudaError_t launch_entry_work(const DevProblem *dp, const WorkEntry *entries, RasterSetup *setup, TetOut *tout,
+                              const int *n_entries_dev, int n_entries_host, cudaStream_t st)
+{
+    k_entry_work<<<grid_for(2LL * n_entries_host), kBlock, 0, st>>>(dp, entries, setup, tout, n_entries_dev,
+                                                                    n_entries_host);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_quads(const DevProblem &hp, int side, void *quad, cudaStream_t st)
+{
+    const long long N = (long long)hp.nx * hp.ny * hp.nz;
+    if (hp.dtype == MOREA_F16)
+        k_build_quads<unsigned short, uint2><<<grid_for(N), kBlock, 0, st>>>(
+            (const unsigned short *)hp.img[side], hp.nx, hp.ny, hp.nz, (uint2 *)quad);
+    else
+        k_build_quads<float, float4><<<grid_for(N), kBlock, 0, st>>>((const float *)hp.img[side], hp.nx, hp.ny,
+                                                                     hp.nz, (float4 *)quad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_band_rows(const DevProblem &hp, int side, short2 *bandrow, cudaStream_t st)
+{
+    k_band_rows<<<grid_for((long long)hp.ny * hp.nz), kBlock, 0, st>>>(hp.band[side], hp.nx, hp.ny, hp.nz, bandrow);
     return cudaGetLastError();
 }
 
@@ -610,9 +705,11 @@ cudaError_t launch_partial_entries(const DevProblem *dp, const DevProblem &hp, i
         if (e != cudaSuccess) return e;
     }
     k_partial_entries<<<n_req, kBlock, smem, st>>>(dp, n_req, slot, chg_off, chg_pts, chg_src, chg_tgt,
-                                                   max_changed, v2t_off, v2t_idx, entries, setup, tout,
-                                                   cap_entries, counter, rinfo, req_chg_pts, req_chg_q);
-    return cudaGetLastError();
+                                                   max_changed, v2t_off, v2t_idx, entries, cap_entries, counter,
+                                                   rinfo, req_chg_pts, req_chg_q);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_entry_work(dp, entries, setup, tout, counter, cap_entries, st);
 }
 
 cudaError_t launch_partial_finalize(const DevProblem *dp, const DevProblem &, int n_req, const ReqInfo *rinfo,

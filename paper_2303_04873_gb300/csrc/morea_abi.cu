@@ -22,6 +22,7 @@ struct morea_problem {
     WorkEntry *entries = nullptr;
     RasterSetup *setup = nullptr;
     RasterOut *rout = nullptr;
+    int2 *bandrows = nullptr;
     TetOut *tout = nullptr;
     int *counter = nullptr;
     ReqInfo *rinfo = nullptr;
@@ -110,7 +111,8 @@ cudaError_t timed_raster(morea_problem *p, const int *n_dev, int n_host, int gri
         cudaError_t r = cudaEventRecord(a, st);
         if (r != cudaSuccess) return r;
     }
-    cudaError_t e = launch_raster(p->dp, p->hp, p->entries, p->setup, p->rout, n_dev, n_host, grid, st);
+    cudaError_t e = launch_raster(p->dp, p->hp, p->entries, p->setup, p->rout, p->bandrows, n_dev, n_host, grid,
+                                  st);
     if (e == cudaSuccess && (p->prof & 1u)) e = cudaEventRecord(b, st);
     if (e == cudaSuccess && (p->prof & 2u)) e = launch_count_visits(p->rout, n_dev, n_host, p->visits, st);
     return e;
@@ -322,6 +324,8 @@ morea_status morea_create_problem(const morea_problem_desc *d, void *stream, mor
     float *dcd = nullptr, *dmap[2] = {nullptr, nullptr};
     float4 *gp_d[2] = {nullptr, nullptr}, *gsort_d = nullptr;
     uint8_t *band[2] = {nullptr, nullptr};
+    unsigned char *quad[2] = {nullptr, nullptr};
+    short2 *bandrow[2] = {nullptr, nullptr};
     int *cs_d[2] = {nullptr, nullptr}, *cp_d[2] = {nullptr, nullptr}, *goff_d = nullptr;
     morea_tet_record *cache = nullptr;
     morea_totals *totals = nullptr;
@@ -347,8 +351,10 @@ morea_status morea_create_problem(const morea_problem_desc *d, void *stream, mor
         TRY(dalloc(p, &gp_d[s], gp[s].size()));
         TRY(dalloc(p, &cs_d[s], cell_start[s].size()));
         TRY(dalloc(p, &cp_d[s], cell_pts[s].size()));
+        TRY(dalloc(p, &quad[s], (size_t)N * esz * 4));
         if (continuous) {
             TRY(dalloc(p, &band[s], (size_t)N));
+            TRY(dalloc(p, &bandrow[s], (size_t)ny * nz));
             if (G > 0) TRY(dalloc(p, &dmap[s], (size_t)N * G));
         }
     }
@@ -361,6 +367,7 @@ morea_status morea_create_problem(const morea_problem_desc *d, void *stream, mor
     TRY(dalloc(p, &p->entries, (size_t)cap));
     TRY(dalloc(p, &p->setup, 2 * (size_t)cap));
     TRY(dalloc(p, &p->rout, 2 * (size_t)cap));
+    if (continuous) TRY(dalloc(p, &p->bandrows, 2 * (size_t)cap * kBandRowsPerItem));
     TRY(dalloc(p, &p->tout, (size_t)cap));
     TRY(dalloc(p, &p->counter, 1));
     TRY(dalloc(p, &p->rinfo, (size_t)max_req));
@@ -376,6 +383,10 @@ morea_status morea_create_problem(const morea_problem_desc *d, void *stream, mor
     hp.dmap[1] = dmap[1];
     hp.band[0] = band[0];
     hp.band[1] = band[1];
+    hp.quad[0] = quad[0];
+    hp.quad[1] = quad[1];
+    hp.bandrow[0] = bandrow[0];
+    hp.bandrow[1] = bandrow[1];
     hp.tets = dtets;
     hp.cdelta = dcd;
     for (int s = 0; s < 2; ++s) {
@@ -416,6 +427,7 @@ morea_status morea_create_problem(const morea_problem_desc *d, void *stream, mor
     TRY(cudaMemsetAsync(p->setup, 0, sizeof(RasterSetup) * 2 * (size_t)cap, st));
     TRY(cudaMemsetAsync(p->rinfo, 0, sizeof(ReqInfo) * (size_t)max_req, st));
     TRY(cudaMemcpyAsync(p->dp, &hp, sizeof(DevProblem), cudaMemcpyHostToDevice, st));
+    for (int s = 0; s < 2; ++s) TRY(launch_build_quads(hp, s, quad[s], st));
     if (continuous && G > 0) {
         for (int s = 0; s < 2; ++s) {
             TRY(cudaMemcpyAsync(gsort_d, gsorted[s].data(), sizeof(float4) * gsorted[s].size(),
@@ -423,6 +435,34 @@ morea_status morea_create_problem(const morea_problem_desc *d, void *stream, mor
             TRY(launch_distance_maps(hp, gsort_d, goff_d, dmap[s], band[s], st));
             TRY(cudaStreamSynchronize(st));   // gsort_d is reused for the other side
         }
+    }
+    if (continuous) {
+        for (int s = 0; s < 2; ++s) TRY(launch_band_rows(hp, s, bandrow[s], st));
+        // per-row sorted lists of band voxels (built on the host from the masks)
+        std::vector<uint8_t> hband((size_t)N);
+        for (int s = 0; s < 2; ++s) {
+            TRY(cudaMemcpyAsync(hband.data(), band[s], (size_t)N, cudaMemcpyDeviceToHost, st));
+            TRY(cudaStreamSynchronize(st));
+            std::vector<int> start((size_t)ny * nz + 1, 0);
+            std::vector<short> xs;
+            for (long long row = 0; row < (long long)ny * nz; ++row) {
+                const uint8_t *b = hband.data() + row * nx;
+                for (int x = 0; x < nx; ++x)
+                    if (b[x]) xs.push_back((short)x);
+                start[row + 1] = (int)xs.size();
+            }
+            int *bs = nullptr;
+            short *bxs = nullptr;
+            TRY(dalloc(p, &bs, start.size()));
+            TRY(dalloc(p, &bxs, std::max<size_t>(xs.size(), 1)));
+            TRY(cudaMemcpyAsync(bs, start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice, st));
+            if (!xs.empty())
+                TRY(cudaMemcpyAsync(bxs, xs.data(), sizeof(short) * xs.size(), cudaMemcpyHostToDevice, st));
+            TRY(cudaStreamSynchronize(st));
+            hp.band_start[s] = bs;
+            hp.band_x[s] = bxs;
+        }
+        TRY(cudaMemcpyAsync(p->dp, &hp, sizeof(DevProblem), cudaMemcpyHostToDevice, st));
     }
     TRY(cudaStreamSynchronize(st));
 #undef TRY

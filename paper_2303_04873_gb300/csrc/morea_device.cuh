@@ -109,9 +109,25 @@ __device__ __forceinline__ void make_setup(const int4 *own, const int4 *oth, con
     su.khi = min(P.nz - 1, floor_shift(mxz - H, kb));
     su.qlo[0] = mnx; su.qlo[1] = mny; su.qlo[2] = mnz;
     su.qhi[0] = mxx; su.qhi[1] = mxy; su.qhi[2] = mxz;
-    su.valid = D > 0.0;
-    su.pad = 0;
+    // the other copy's bounding box strictly inside [0, n-1] (margin 1/64
+    // voxel, far above the FP32 error of a mapped position): then the
+    // trilinear sample needs no clamping
+    bool inner = true;
+    {
+        const int om[3] = {min(min(oth[0].x, oth[1].x), min(oth[2].x, oth[3].x)),
+                           min(min(oth[0].y, oth[1].y), min(oth[2].y, oth[3].y)),
+                           min(min(oth[0].z, oth[1].z), min(oth[2].z, oth[3].z))};
+        const int oM[3] = {max(max(oth[0].x, oth[1].x), max(oth[2].x, oth[3].x)),
+                           max(max(oth[0].y, oth[1].y), max(oth[2].y, oth[3].y)),
+                           max(max(oth[0].z, oth[1].z), max(oth[2].z, oth[3].z))};
+        const int n[3] = {P.nx, P.ny, P.nz};
+        const int margin = max(1, P.S >> 6);
+        for (int a = 0; a < 3; ++a)
+            inner = inner && om[a] - H >= margin && oM[a] - H <= (n[a] - 1) * P.S - margin;
+    }
+    su.valid = (D > 0.0 ? 1 : 0) | (inner ? 2 : 0);
     const long long S = P.S;
+    const int nyb1 = max(0, su.jhi - su.jlo), nzb1 = max(0, su.khi - su.klo);
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
         int4 w0 = own[f == 0 ? 1 : 0];
@@ -127,20 +143,25 @@ __device__ __forceinline__ void make_setup(const int4 *own, const int4 *oth, con
         long long tie = (nx > 0 || (nx == 0 && (ny > 0 || (ny == 0 && nz > 0)))) ? 1 : 0;
         long long ct = c + tie;
         su.ct[f] = ct;
-        su.ax[f] = nx * S;
-        su.by[f] = ny * S;
-        su.bz[f] = nz * S;
-        long long b0 = ct + (nx + ny + nz) * (long long)H;
-        long long b00 = b0 + su.by[f] * su.jlo + su.bz[f] * su.klo;
-        su.b00[f] = b00;
+        FaceRow fr;
+        fr.ax = nx * S;
+        fr.by = ny * S;
+        fr.bz = nz * S;
+        fr.b00 = ct + (nx + ny + nz) * (long long)H + fr.by * su.jlo + fr.bz * su.klo;
         if (nx != 0) {
-            double inv = -1.0 / (double)su.ax[f];
-            su.e0[f] = (float)((double)b00 * inv);
-            su.ey[f] = (float)((double)su.by[f] * inv);
-            su.ez[f] = (float)((double)su.bz[f] * inv);
+            double inv = -1.0 / (double)fr.ax;
+            fr.e0 = (float)((double)fr.b00 * inv);
+            fr.ey = (float)((double)fr.by * inv);
+            fr.ez = (float)((double)fr.bz * inv);
+            // |estimate - root| <= 2^-24 (3 |e0| + 3 |ey| dj + 3 |ez| dk) (rounding
+            // of e0, ey, ez and of the two FMAs); 2^-20 leaves a factor 5 margin
+            fr.tol = (fabsf(fr.e0) + fabsf(fr.ey) * (float)nyb1 + fabsf(fr.ez) * (float)nzb1 + 1.0f) *
+                     (1.0f / 1048576.0f);
         } else {
-            su.e0[f] = su.ey[f] = su.ez[f] = 0.0f;
+            fr.e0 = fr.ey = fr.ez = 0.0f;
+            fr.tol = 0.0f;
         }
+        su.f[f] = fr;
     }
     // affine map own -> other: M = F E^-1, E = [e1 e2 e3] edge columns of the
     // own copy, rows of E^-1 = (e2 x e3, e3 x e1, e1 x e2) / D (exact int64

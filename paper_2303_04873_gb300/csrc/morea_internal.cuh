@@ -2,6 +2,8 @@
 // Not part of the public ABI (include/morea.h).
 #pragma once
 
+#include <cstddef>
+
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -23,8 +25,12 @@ struct DevProblem {
     int n_guid, cshift;
     float wgt[kMaxGroups];           // |C^k| / |G| per guidance group
     const void *img[2];              // [0] source image I_s, [1] target image I_t
+    const void *quad[2];             // per voxel (x,y),(x+1,y),(x,y+1),(x+1,y+1) of the same z-plane
     const float *dmap[2];            // [G][N] distance maps of the source / target contours
     const uint8_t *band[2];          // [N] bit g set where dmap[side][g] < r
+    const short2 *bandrow[2];        // [nz*ny] x-range of band voxels in each image row (empty: x > y)
+    const int *band_start[2];        // [nz*ny + 1] CSR of the band voxels of each image row
+    const short *band_x[2];          // their x, ascending within a row
     const int4 *tets;                // positively oriented topology
     const float *cdelta;             // elasticity factor per tet
     const int4 *gq[2];               // snapped guidance points per side
@@ -44,20 +50,37 @@ struct __align__(16) WorkEntry {
     int4 q[2][4];                    // [mesh: 0 source, 1 target][vertex]
 };
 
+// One face f of a tet copy as a function of the voxel row (j, k): the voxel
+// centre (i, j, k) is inside w.r.t. f iff  ax i + b00 + by dj + bz dk > 0
+// (dj = j - jlo, dk = k - klo; integers, simulation-of-simplicity tie bit
+// folded into b00).  e0 + ey dj + ez dk estimates the root -B/A in FP32 to
+// within tol for every row of the bounding box (a rigorous bound).
+struct __align__(16) FaceRow {
+    long long ax, b00, by, bz;
+    float e0, ey, ez, tol;
+};
+
 // Per (entry, side) rasterisation set-up, written by the tet pass.
-// Face f of the own copy: g_f . P + c_f + tie_f > 0 for P strictly inside
-// after the symbolic perturbation.  For voxel rows (j, k) of the own image,
-// with dj = j - jlo, dk = k - klo:   A_f i + B00_f + By_f dj + Bz_f dk > 0.
 struct __align__(16) RasterSetup {
-    long long ax[4], by[4], bz[4], b00[4];
-    long long ct[4];                 // c_f + tie_f (for arbitrary snapped points)
-    float e0[4], ey[4], ez[4];       // float estimate of the root -B/A in voxel index
-    float M[9];                      // affine map own -> other, row-major
-    float s0[3], t0[3];              // vertex 0 of the own / other copy, voxel units
+    FaceRow f[4];
+    long long ct[4];                 // c_f + tie_f (inside test of arbitrary snapped points)
+    float M[9];                      // affine map own -> other, row-major, voxel units
+    float s0[3];                     // vertex 0 of the own copy
+    float t0[3];                     // vertex 0 of the other copy
+    int valid;                         // bit 0: orientation > 0; bit 1: the other copy lies
+                                       // strictly inside [0, n-1] (no sample clamping needed)
     int ilo, ihi, jlo, jhi, klo, khi;  // voxel-centre index range of the bounding box
     int qlo[3], qhi[3];                // snapped bounding box
-    int valid, pad;
 };
+
+// k_raster reads the set-up with vector loads at these offsets
+static_assert(sizeof(FaceRow) == 48, "FaceRow layout");
+static_assert(offsetof(RasterSetup, M) % 16 == 0, "M must start a 16-byte word");
+static_assert(offsetof(RasterSetup, s0) == offsetof(RasterSetup, M) + 36, "M[8], s0 share a word");
+static_assert(offsetof(RasterSetup, t0) % 16 == 0, "t0 must start a 16-byte word");
+static_assert(offsetof(RasterSetup, valid) == offsetof(RasterSetup, t0) + 12, "t0, valid share a word");
+static_assert(offsetof(RasterSetup, ilo) % 16 == 0, "ilo..jhi form one int4");
+static_assert(offsetof(RasterSetup, klo) % 8 == 0, "klo, khi form one int2");
 
 struct __align__(16) RasterOut {
     float e_img, e_guid;
@@ -83,8 +106,14 @@ cudaError_t launch_snap_slots(const DevProblem *dp, const DevProblem &hp, int n_
                               cudaStream_t st);
 cudaError_t launch_full_entries(const DevProblem *dp, const DevProblem &hp, int n_sol, const int *slot,
                                 WorkEntry *entries, RasterSetup *setup, TetOut *tout, cudaStream_t st);
+cudaError_t launch_entry_work(const DevProblem *dp, const WorkEntry *entries, RasterSetup *setup, TetOut *tout,
+                              const int *n_entries_dev, int n_entries_host, cudaStream_t st);
+cudaError_t launch_build_quads(const DevProblem &hp, int side, void *quad, cudaStream_t st);
+cudaError_t launch_band_rows(const DevProblem &hp, int side, short2 *bandrow, cudaStream_t st);
+// image pass (+ continuous guidance pass); bandrows: [2 * entries][kBandRowsPerItem] scratch
+constexpr int kBandRowsPerItem = 128;
 cudaError_t launch_raster(const DevProblem *probs, const DevProblem &hp, const WorkEntry *entries,
-                          const RasterSetup *setup, RasterOut *rout, const int *n_entries_dev,
+                          const RasterSetup *setup, RasterOut *rout, int2 *bandrows, const int *n_entries_dev,
                           int n_entries_host, int grid, cudaStream_t st);
 cudaError_t launch_reduce_full(const DevProblem *dp, const DevProblem &hp, int n_sol, const int *slot,
                                const TetOut *tout, const RasterOut *rout, double *obj, uint8_t *folded,
