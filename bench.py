@@ -38,7 +38,8 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 ROUNDS = 20
-BYTES_PER_VISIT_F32 = 8          # own voxel + one amortised voxel of the other image, 4 B each
+# algorithmic bytes per voxel visit: the own voxel + one amortised voxel of the
+# other image, b bytes each (b = 4 for FP32 storage, 2 for FP16)
 L2_FLUSH_BYTES = 512 << 20       # > 129 MB L2
 
 
@@ -49,12 +50,23 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["c1", "c2", "c4"], default="c1",
+                    help="c1: 128x128x96 f32 (the headline); c2: 256x256x160 f16 graded mesh; "
+                         "c4: 16 uneven f16 problems in one batched graph launch")
     return ap.parse_args()
 
 
-def workload(seed_offset=0):
+WORKLOADS = {
+    "c1": ("c1: 128x128x96 f32 images, 567 pts / 2304 tets, population 128, "
+           "1 full eval + 20 partial rounds (4-32 pts) with commits per step", 4),
+    "c2": ("c2: 256x256x160 f16 images (HU-like), graded 1521 pts / 6912 tets, population 256, "
+           "1 full eval + 20 partial rounds (4-32 pts) with commits per step", 2),
+}
+
+
+def workload(seed_offset=0, name="c1"):
     import synth
-    p = synth.make_c1()
+    p = synth.make_c1() if name == "c1" else synth.make_c2()
     adj = synth.vertex_adjacency(p.tets, p.n_points)
     rounds = synth.partial_requests(p, adj, ROUNDS, 4, 32, 1.0, 3 + seed_offset)
     rng = np.random.default_rng(4 + seed_offset)
@@ -123,7 +135,7 @@ def oracle_sample(orc, p, rounds, cores):
     """Time the FP64 oracle on a bounded sample of the step: `cores` full
     evaluations and 4 x `cores` partial evaluations of the first round, run
     over `cores` threads (each oracle call releases the GIL).  Returns
-    (evals/s for the step's mix of 128 full + 2560 partial evaluations,
+    (evals/s for the step's mix of full and partial evaluations,
     description, seconds per full, seconds per partial)."""
     n_full = max(cores, 2)
     sols = list(range(n_full))
@@ -149,8 +161,9 @@ def oracle_sample(orc, p, rounds, cores):
     n_sol = p.n_solutions
     step_s = n_sol * t_full + ROUNDS * n_sol * t_part
     evals = n_sol + ROUNDS * n_sol
-    desc = (f"{n_full} full + {len(reqs)} partial oracle evaluations of the 128x128x96 problem on {cores} threads; "
-            f"{t_full * 1e3:.0f} ms/full, {t_part * 1e3:.1f} ms/partial (wall, parallel); step = 128 full + 2560 partial")
+    desc = (f"{n_full} full + {len(reqs)} partial oracle evaluations of the {p.nx}x{p.ny}x{p.nz} problem on "
+            f"{cores} threads; {t_full * 1e3:.0f} ms/full, {t_part * 1e3:.1f} ms/partial (wall, parallel); "
+            f"step = {n_sol} full + {ROUNDS * n_sol} partial")
     return evals / step_s, desc, t_full, t_part
 
 
@@ -160,7 +173,7 @@ def run_reference(args):
         return 0
     import oracle
     cores = os.cpu_count() or 1
-    p, rounds, accept = workload()
+    p, rounds, accept = workload(name=args.workload)
     orc = oracle.Oracle(p)
     per_step = []
     desc = ""
@@ -175,8 +188,7 @@ def run_reference(args):
         "impl": "reference", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": evals / value * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "c1: 128x128x96 f32, 567 pts / 2304 tets, population 128, 20 partial rounds",
-                   "l2": "n/a (CPU)"},
+        "config": {"workload": WORKLOADS[args.workload][0], "l2": "n/a (CPU)"},
         "cpu_baseline": {"value": value, "unit": "solution-evals/s", "cores": cores, "kind": "oracle",
                          "sample": desc},
         "e2e": {"value": value, "unit": "solution-evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -210,7 +222,8 @@ def run_ours(args):
     from paper_2303_04873_gb300 import morea
 
     # the oracle sample runs first, on host threads, before any GPU work
-    p, rounds, accept = workload()
+    p, rounds, accept = workload(name=args.workload)
+    bytes_per_visit = 2 * WORKLOADS[args.workload][1]
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
@@ -345,21 +358,20 @@ def run_ours(args):
     e2e_value = world * evals_per_step * args.steps / (e2e_total / 1e3)
 
     peak, peak_kind = peaks()
-    achieved = visits_per_step * args.steps * BYTES_PER_VISIT_F32 / (raster_ms / 1e3) / 1e9
+    achieved = visits_per_step * args.steps * bytes_per_visit / (raster_ms / 1e3) / 1e9
     line = {
         "metric": "solution-evals/sec (full & partial)", "value": value, "unit": "solution-evals/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "c1: 128x128x96 f32 images, 567 pts / 2304 tets, population 128, "
-                               "1 full eval + 20 partial rounds (4-32 pts) with commits per step",
+        "config": {"workload": WORKLOADS[args.workload][0],
                    "evals_per_step": evals_per_step, "l2": "flushed before every timed step (512 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None,
                      "kernel": "k_raster (rasterise + map + trilinear + h + guidance)",
                      "peak_kind": f"{peak_kind} copy bandwidth",
-                     "algorithmic_bytes": f"{BYTES_PER_VISIT_F32} B per voxel visit x {visits_per_step} visits/step",
+                     "algorithmic_bytes": f"{bytes_per_visit} B per voxel visit x {visits_per_step} visits/step",
                      "kernel_ms_per_step": raster_ms / args.steps, "launches": raster_launches},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "solution-evals/s", "h2d_bytes_per_step": int(h2d),
@@ -379,10 +391,107 @@ def run_ours(args):
     return 0
 
 
+def run_batch(args):
+    """16 problems of uneven sizes (64^3 .. 192x192x128 f16, 200-1500 points,
+    populations 32-256): full evaluation of every population in one batched
+    evaluation (one launch per kernel), captured once as a CUDA graph and
+    replayed; the launch shape comes from the autotuner."""
+    import torch
+    import synth
+    from paper_2303_04873_gb300 import build as _b
+    _b.build()
+    from paper_2303_04873_gb300 import autotune, morea
+    torch.cuda.set_device(0)
+    probs = synth.make_c4()
+    gps = [morea.Problem(p) for p in probs]
+    batch = morea.Batch(gps)
+    dev = torch.device("cuda", 0)
+    srcs = [torch.as_tensor(p.sol_src).to(dev) for p in probs]
+    tgts = [torch.as_tensor(p.sol_tgt).to(dev) for p in probs]
+    outs = morea.Batch.outputs(srcs)
+    n_total = sum(p.n_solutions for p in probs)
+    key = autotune.signature(gps, [p.n_solutions for p in probs], "batch_full")
+    bps, chunk, timings = autotune.tune(batch, lambda: batch.eval_full(srcs, tgts, outs), key)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        batch.capture(srcs, tgts, outs, stream)
+        for _ in range(max(3, args.warmup)):
+            batch.replay(stream)
+    stream.synchronize()
+    visits = sum(int(gp.read_totals(p.n_solutions)["n_vox"].sum()) for gp, p in zip(gps, probs))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    replays = max(args.steps, 100)
+    clocks = ClockSampler(0)
+    lat = []
+    for _ in range(replays):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            batch.replay(stream)
+            b.record(stream)
+        b.synchronize()
+        lat.append(a.elapsed_time(b))
+    ck = clocks.stop()
+    lat = np.asarray(lat)
+    mean_ms = float(lat.mean())
+    # e2e: host inputs copied into the captured buffers, replay, outputs copied back
+    h_src = [s.cpu().pin_memory() for s in srcs]
+    h_tgt = [t.cpu().pin_memory() for t in tgts]
+    h_out = [[o.cpu().pin_memory() for o in oo] for oo in outs]
+    e2e = []
+    for _ in range(max(args.steps, 10)):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for d, h in zip(srcs + tgts, h_src + h_tgt):
+                d.copy_(h, non_blocking=True)
+            batch.replay(stream)
+            for ho, do in zip(h_out, outs):
+                for h, d in zip(ho, do):
+                    h.copy_(d, non_blocking=True)
+            b.record(stream)
+        b.synchronize()
+        e2e.append(a.elapsed_time(b))
+    h2d = sum(t.numel() * 4 for t in h_src + h_tgt)
+    d2h = sum(t.numel() * t.element_size() for oo in h_out for t in oo)
+    peak, peak_kind = peaks()
+    achieved = visits * 4 / (mean_ms / 1e3) / 1e9
+    line = {
+        "metric": "solution-evals/sec (full & partial)", "value": n_total / (mean_ms / 1e3),
+        "unit": "solution-evals/s", "n_gpus": 1, "steps": replays, "warmup": args.warmup,
+        "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "c4: 16 problems 64^3..192x192x128 f16, 200-1512 points, populations 32-256 "
+                               f"({n_total} solutions), one batched full evaluation per graph replay",
+                   "launch": {"blocks_per_sm": bps, "chunk": chunk, "tuned": {f"{k[0]},{k[1]}": v
+                                                                            for k, v in timings.items()}},
+                   "l2": "flushed before every replay (512 MiB write)"},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "replays": replays,
+                       "note": "every problem of the batch completes within one replay"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "whole batched evaluation (graph replay)",
+                     "peak_kind": f"{peak_kind} copy bandwidth",
+                     "algorithmic_bytes": f"4 B per voxel visit x {visits} visits/replay"},
+        "cpu_baseline": None,
+        "e2e": {"value": n_total / (float(np.mean(e2e)) / 1e3), "unit": "solution-evals/s",
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": 7 * replays,
+        "clocks": ck,
+        "voxel_visits_per_s": visits / (mean_ms / 1e3),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "c4":
+        return run_batch(args)
     return run_ours(args)
 
 

@@ -215,6 +215,54 @@ morea_status morea_device_status(morea_problem *p, void *stream, uint32_t *bits)
 morea_status morea_problem_info(const morea_problem *p, int32_t *n_points, int32_t *n_tets,
                                 int32_t *n_groups, double *trunc_radius, int32_t *subvoxel_bits);
 
+/* ---- batched multi-problem evaluation (one launch per kernel for all) ---- */
+
+typedef struct morea_batch morea_batch;                 /* opaque handle */
+
+/* Maximum number of problems in one batch. */
+#define MOREA_MAX_BATCH 64
+
+/* Group n_problems (1..MOREA_MAX_BATCH) distinct problems created on the same
+ * device with the same storage type, h_mode and g_mode, so that one launch of
+ * each kernel evaluates all of them: the work entries of all problems form
+ * one list that the image pass walks as a single persistent launch.
+ * Allocates the batch's own scratch (sum over problems of max_solutions x
+ * n_tets work entries).  The problems must outlive the batch; the batch
+ * writes slots 0..n_sol[i]-1 of problem i. */
+morea_status morea_batch_create(morea_problem *const *problems, int32_t n_problems, morea_batch **out);
+
+/* Frees the batch's scratch and graph (not the problems).  NULL is a no-op. */
+morea_status morea_batch_destroy(morea_batch *b);
+
+/* Full evaluation (Sec. 4.1) of n_sol[i] solutions of every problem i of the
+ * batch, as morea_eval_full with slots 0..n_sol[i]-1, with one launch per
+ * kernel for the whole batch.  All pointer arguments are host arrays of
+ * n_problems device pointers (severity may be NULL, or hold NULL entries).
+ * Results are identical to per-problem morea_eval_full calls. */
+morea_status morea_batch_eval_full(morea_batch *b, const int32_t *n_sol, const float *const *src_pts,
+                                   const float *const *tgt_pts, double *const *obj,
+                                   uint8_t *const *folded, double *const *severity, void *stream);
+
+/* Record one morea_batch_eval_full with these arguments into a CUDA graph
+ * held by the batch (replacing any previous one); `stream` must be a
+ * non-default stream, used for the capture only.  The graph keeps the device
+ * pointers and sizes given here and the launch shape in force now. */
+morea_status morea_batch_capture(morea_batch *b, const int32_t *n_sol, const float *const *src_pts,
+                                 const float *const *tgt_pts, double *const *obj,
+                                 uint8_t *const *folded, double *const *severity, void *stream);
+
+/* Launch the captured graph on `stream` (the evaluation reads the current
+ * contents of the captured input buffers).  MOREA_EINVAL if none captured. */
+morea_status morea_batch_replay(morea_batch *b, void *stream);
+
+/* Launch shape of the image and guidance passes, normally chosen by the
+ * autotuner (paper_2303_04873_gb300.autotune): blocks_per_sm in [1, 64]
+ * (grid = blocks_per_sm x SM count) and chunk in [0, 1024]: 0 = static
+ * striding of (tet, side) items over warps, > 0 = warps take `chunk` items
+ * at a time from an atomic work queue.  Results do not depend on it. */
+morea_status morea_set_launch(morea_problem *p, int32_t blocks_per_sm, int32_t chunk);
+morea_status morea_batch_set_launch(morea_batch *b, int32_t blocks_per_sm, int32_t chunk);
+
 /* Instrumentation for benchmarks (not a step of the method; the paper has no
  * counterpart).  flags bit 0: record a CUDA event pair on the call's stream
  * around every launch of the rasterisation/sampling kernel (the hot loop);

@@ -275,6 +275,29 @@ __device__ __forceinline__ void guidance_pairs(const DevProblem &P, const Raster
             }
 }
 
+// Item scheduling of the image and guidance passes: static striding of the
+// (entry, side) items over all warps, or (chunk > 0) a work queue from which
+// each warp takes `chunk` consecutive items with one atomic add, so warps that
+// drew large tets do not hold up the tail of an uneven batch.
+template <typename F>
+__device__ __forceinline__ void run_items(int n_items, int chunk, int *queue, F &&body)
+{
+    const int lane = threadIdx.x & 31;
+    if (chunk <= 0) {
+        const int wpb = blockDim.x >> 5;
+        for (int item = blockIdx.x * wpb + (threadIdx.x >> 5); item < n_items; item += gridDim.x * wpb) body(item);
+        return;
+    }
+    for (;;) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(queue, chunk);
+        base = __shfl_sync(FULL, base, 0);
+        if (base >= n_items) break;
+        const int end = min(base + chunk, n_items);
+        for (int item = base; item < end; ++item) body(item);
+    }
+}
+
 // Pass modes of the image kernel.
 constexpr int kPassImage = 0;       // f_intensity only
 constexpr int kPassImageBand = 1;   // f_intensity + record the rows that touch a guidance band
@@ -296,15 +319,14 @@ __global__ void __launch_bounds__(kBlock, 4) k_raster(const DevProblem *__restri
                                                      const WorkEntry *__restrict__ entries,
                                                      const RasterSetup *__restrict__ setup,
                                                      RasterOut *__restrict__ rout, int2 *__restrict__ bandrows,
-                                                     const int *n_entries_dev, int n_entries_host)
+                                                     const int *n_entries_dev, int n_entries_host, int chunk,
+                                                     int *queue)
 {
     using QT = typename QuadOf<TI>::T;
     const int lane = threadIdx.x & 31;
     const int n_ent = n_entries_dev ? min(*n_entries_dev, n_entries_host) : n_entries_host;
     const int n_items = 2 * n_ent;
-    const int wpb = blockDim.x >> 5;
-    const int nwarps = gridDim.x * wpb;
-    for (int item = blockIdx.x * wpb + (threadIdx.x >> 5); item < n_items; item += nwarps) {
+    run_items(n_items, chunk, queue, [&](const int item) {
         const int side = item >= n_ent ? 1 : 0;      // all source sides first, then all target sides
         const int e = item - side * n_ent;
         const RasterSetup *su = setup + 2 * (size_t)e + side;
@@ -413,7 +435,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_raster(const DevProblem *__restri
             ro.n_gp = ngp;
             rout[2 * (size_t)e + side] = ro;
         }
-    }
+    });
 }
 
 // Continuous guidance (a6): for every (entry, side) with band rows, the band
@@ -426,19 +448,17 @@ __global__ void __launch_bounds__(kBlock, 4) k_guidance(const DevProblem *__rest
                                                        const RasterSetup *__restrict__ setup,
                                                        RasterOut *__restrict__ rout,
                                                        const int2 *__restrict__ bandrows, const int *n_entries_dev,
-                                                       int n_entries_host)
+                                                       int n_entries_host, int chunk, int *queue)
 {
     const int lane = threadIdx.x & 31;
     const int n_ent = n_entries_dev ? min(*n_entries_dev, n_entries_host) : n_entries_host;
     const int n_items = 2 * n_ent;
-    const int wpb = blockDim.x >> 5;
-    const int nwarps = gridDim.x * wpb;
-    for (int item = blockIdx.x * wpb + (threadIdx.x >> 5); item < n_items; item += nwarps) {
+    run_items(n_items, chunk, queue, [&](const int item) {
         const int side = item >= n_ent ? 1 : 0;
         const int e = item - side * n_ent;
         RasterOut *ro = rout + 2 * (size_t)e + side;
         const int nband = ro->n_gp;                   // warp-uniform
-        if (nband == 0) continue;
+        if (nband == 0) return;
         const RasterSetup *su = setup + 2 * (size_t)e + side;
         const unsigned char *sb = reinterpret_cast<const unsigned char *>(su);
         const float4 m0 = __ldg(reinterpret_cast<const float4 *>(sb + offsetof(RasterSetup, M)));
@@ -540,27 +560,29 @@ __global__ void __launch_bounds__(kBlock, 4) k_guidance(const DevProblem *__rest
             ro->e_guid = e_g;
             ro->n_gp = 0;
         }
-    }
+    });
 }
 
 template <typename TI, int HMODE>
 cudaError_t launch_g(const DevProblem *probs, int g_mode, const WorkEntry *entries, const RasterSetup *setup,
-                     RasterOut *rout, int2 *bandrows, const int *n_dev, int n_host, int grid, cudaStream_t st)
+                     RasterOut *rout, int2 *bandrows, const int *n_dev, int n_host, int grid, int chunk, int *queue,
+                     cudaStream_t st)
 {
     switch (g_mode) {
     case MOREA_G_CONTINUOUS:
         k_raster<TI, HMODE, kPassImageBand><<<grid, kBlock, 0, st>>>(probs, entries, setup, rout, bandrows, n_dev,
-                                                                    n_host);
+                                                                    n_host, chunk, queue);
         if (cudaPeekAtLastError() == cudaSuccess)
-            k_guidance<<<grid, kBlock, 0, st>>>(probs, entries, setup, rout, bandrows, n_dev, n_host);
+            k_guidance<<<grid, kBlock, 0, st>>>(probs, entries, setup, rout, bandrows, n_dev, n_host, chunk,
+                                                queue + 1);
         break;
     case MOREA_G_PAIR_TRANSFER:
         k_raster<TI, HMODE, kPassImagePairs><<<grid, kBlock, 0, st>>>(probs, entries, setup, rout, bandrows, n_dev,
-                                                                     n_host);
+                                                                     n_host, chunk, queue);
         break;
     default:
         k_raster<TI, HMODE, kPassImage><<<grid, kBlock, 0, st>>>(probs, entries, setup, rout, bandrows, n_dev,
-                                                                n_host);
+                                                                n_host, chunk, queue);
         break;
     }
     return cudaGetLastError();
@@ -570,21 +592,25 @@ cudaError_t launch_g(const DevProblem *probs, int g_mode, const WorkEntry *entri
 
 cudaError_t launch_raster(const DevProblem *probs, const DevProblem &hp, const WorkEntry *entries,
                           const RasterSetup *setup, RasterOut *rout, int2 *bandrows, const int *n_entries_dev,
-                          int n_entries_host, int grid, cudaStream_t st)
+                          int n_entries_host, int grid, int chunk, int *queue, cudaStream_t st)
 {
     if (grid <= 0) grid = sm_count() * 8;
+    if (chunk > 0) {
+        cudaError_t e = cudaMemsetAsync(queue, 0, 2 * sizeof(int), st);
+        if (e != cudaSuccess) return e;
+    }
     if (hp.dtype == MOREA_F16) {
         if (hp.h_mode == MOREA_H_MOREA_FG)
             return launch_g<__half, MOREA_H_MOREA_FG>(probs, hp.g_mode, entries, setup, rout, bandrows, n_entries_dev,
-                                                      n_entries_host, grid, st);
+                                                      n_entries_host, grid, chunk, queue, st);
         return launch_g<__half, MOREA_H_PLAIN_SSD>(probs, hp.g_mode, entries, setup, rout, bandrows, n_entries_dev,
-                                                   n_entries_host, grid, st);
+                                                   n_entries_host, grid, chunk, queue, st);
     }
     if (hp.h_mode == MOREA_H_MOREA_FG)
         return launch_g<float, MOREA_H_MOREA_FG>(probs, hp.g_mode, entries, setup, rout, bandrows, n_entries_dev,
-                                                 n_entries_host, grid, st);
+                                                 n_entries_host, grid, chunk, queue, st);
     return launch_g<float, MOREA_H_PLAIN_SSD>(probs, hp.g_mode, entries, setup, rout, bandrows, n_entries_dev,
-                                              n_entries_host, grid, st);
+                                              n_entries_host, grid, chunk, queue, st);
 }
 
 }  // namespace morea

@@ -7,68 +7,11 @@
 #include <new>
 #include <vector>
 
-#include "morea_internal.cuh"
+#include "morea_host.h"
 
 using namespace morea;
 
-struct morea_problem {
-    int device = 0;
-    DevProblem hp{};
-    DevProblem *dp = nullptr;
-    std::vector<void *> allocs;
-    int V = 0, T = 0, G = 0, max_sol = 0, max_req = 0, max_changed = 0, max_star = 0;
-    int cap_entries = 0;
-    int *v2t_off = nullptr, *v2t_idx = nullptr;
-    WorkEntry *entries = nullptr;
-    RasterSetup *setup = nullptr;
-    RasterOut *rout = nullptr;
-    int2 *bandrows = nullptr;
-    TetOut *tout = nullptr;
-    int *counter = nullptr;
-    ReqInfo *rinfo = nullptr;
-    morea_totals *req_delta = nullptr;
-    int *req_chg_pts = nullptr;
-    int4 *req_chg_q = nullptr;
-    int last_nreq = 0;
-    double r = 0.0;
-    // instrumentation (morea_profile)
-    unsigned prof = 0;
-    std::vector<cudaEvent_t> ev;
-    size_t ev_used = 0;
-    unsigned long long *visits = nullptr;
-};
-
 namespace {
-
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev)
-    {
-        int cur = 0;
-        if (cudaGetDevice(&cur) == cudaSuccess && cur != dev) {
-            prev = cur;
-            cudaSetDevice(dev);
-        }
-    }
-    ~DeviceGuard()
-    {
-        if (prev >= 0) cudaSetDevice(prev);
-    }
-};
-
-template <typename T>
-cudaError_t dalloc(morea_problem *p, T **ptr, size_t count)
-{
-    void *m = nullptr;
-    cudaError_t e = cudaMalloc(&m, std::max<size_t>(count, 1) * sizeof(T));
-    if (e != cudaSuccess) {
-        *ptr = nullptr;
-        return e;
-    }
-    p->allocs.push_back(m);
-    *ptr = (T *)m;
-    return cudaSuccess;
-}
 
 // Same snapping rule as the kernels: clamp to [-0.5, n-0.5], then
 // rint(x 2^k) + 2^(k-1), round half to even.
@@ -112,7 +55,7 @@ cudaError_t timed_raster(morea_problem *p, const int *n_dev, int n_host, int gri
         if (r != cudaSuccess) return r;
     }
     cudaError_t e = launch_raster(p->dp, p->hp, p->entries, p->setup, p->rout, p->bandrows, n_dev, n_host, grid,
-                                  st);
+                                  p->launch.chunk, p->queue, st);
     if (e == cudaSuccess && (p->prof & 1u)) e = cudaEventRecord(b, st);
     if (e == cudaSuccess && (p->prof & 2u)) e = launch_count_visits(p->rout, n_dev, n_host, p->visits, st);
     return e;
@@ -376,6 +319,7 @@ morea_status morea_create_problem(const morea_problem_desc *d, void *stream, mor
     TRY(dalloc(p, &p->req_chg_q, 2 * (size_t)max_req * max_changed));
     TRY(dalloc(p, &p->dp, 1));
     TRY(dalloc(p, &p->visits, 1));
+    TRY(dalloc(p, &p->queue, 2));
 
     hp.img[0] = img[0];
     hp.img[1] = img[1];
@@ -488,7 +432,7 @@ morea_status morea_eval_full(morea_problem *p, int32_t n_sol, const int32_t *slo
         e = launch_full_entries(p->dp, p->hp, n_sol, slot, p->entries, p->setup, p->tout, st);
     if (e == cudaSuccess) {
         const long long items = 2LL * n_sol * p->T;
-        const int grid = (int)std::min<long long>((long long)sm_count() * 8, (items + 7) / 8);
+        const int grid = (int)std::min<long long>((long long)sm_count() * p->launch.blocks_per_sm, (items + 7) / 8);
         e = timed_raster(p, nullptr, n_sol * p->T, grid, st);
     }
     if (e == cudaSuccess)
@@ -511,7 +455,7 @@ morea_status morea_eval_partial(morea_problem *p, int32_t n_req, const int32_t *
                                    p->max_changed, p->v2t_off, p->v2t_idx, p->entries, p->setup, p->tout,
                                    p->cap_entries, p->counter, p->rinfo, p->req_chg_pts, p->req_chg_q, st);
     if (e == cudaSuccess)
-        e = timed_raster(p, p->counter, p->cap_entries, sm_count() * 8, st);
+        e = timed_raster(p, p->counter, p->cap_entries, sm_count() * p->launch.blocks_per_sm, st);
     if (e == cudaSuccess)
         e = launch_partial_finalize(p->dp, p->hp, n_req, p->rinfo, p->entries, p->tout, p->rout, p->req_delta, obj,
                                     folded, severity, st);

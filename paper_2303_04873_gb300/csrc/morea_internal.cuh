@@ -97,8 +97,34 @@ struct ReqInfo {
     int base, count, err, slot, nchg, pad0, pad1, pad2;
 };
 
+// One problem's share of a batched full evaluation (morea_batch_*): its
+// inputs and outputs and where its work sits in the batch's flattened lists.
+struct BatchProb {
+    const float *src, *tgt;          // [n_sol][V][3]
+    double *obj;                     // [n_sol][3]
+    uint8_t *folded;                 // [n_sol]
+    double *severity;                // [n_sol] or NULL
+    long long vert_off;              // first (solution, vertex) of the problem
+    long long entry_off;             // first (solution, tet) entry of the problem
+    int sol_off;                     // first solution of the problem
+    int n_sol;
+};
+
+constexpr int kMaxBatch = 64;
+
+// Passed by value to the batch kernels (kernel parameters are copied at
+// launch, so no host buffer has to outlive the call or a captured graph).
+struct BatchTable {
+    int n;
+    int pad;
+    long long total_verts, total_entries;
+    int total_sols;
+    int pad2;
+    BatchProb p[kMaxBatch];
+};
+
 // ---------------------------------------------------------------------------
-// launch wrappers (k_tet.cu, k_raster.cu)
+// launch wrappers (k_tet.cu, k_raster.cu, k_batch.cu)
 // ---------------------------------------------------------------------------
 
 cudaError_t launch_snap_slots(const DevProblem *dp, const DevProblem &hp, int n_sol, const int *slot,
@@ -112,9 +138,10 @@ cudaError_t launch_build_quads(const DevProblem &hp, int side, void *quad, cudaS
 cudaError_t launch_band_rows(const DevProblem &hp, int side, short2 *bandrow, cudaStream_t st);
 // image pass (+ continuous guidance pass); bandrows: [2 * entries][kBandRowsPerItem] scratch
 constexpr int kBandRowsPerItem = 128;
+// chunk > 0 selects the atomic work queue (queue: 2 device counters, reset here)
 cudaError_t launch_raster(const DevProblem *probs, const DevProblem &hp, const WorkEntry *entries,
                           const RasterSetup *setup, RasterOut *rout, int2 *bandrows, const int *n_entries_dev,
-                          int n_entries_host, int grid, cudaStream_t st);
+                          int n_entries_host, int grid, int chunk, int *queue, cudaStream_t st);
 cudaError_t launch_reduce_full(const DevProblem *dp, const DevProblem &hp, int n_sol, const int *slot,
                                const TetOut *tout, const RasterOut *rout, double *obj, uint8_t *folded,
                                double *severity, cudaStream_t st);
@@ -144,6 +171,11 @@ cudaError_t launch_distance_maps(const DevProblem &hp, const float4 *pts, const 
 
 cudaError_t launch_count_visits(const RasterOut *rout, const int *n_entries_dev, int n_entries_host,
                                 unsigned long long *visits, cudaStream_t st);
+
+cudaError_t launch_batch_snap(const DevProblem *probs, const BatchTable &tb, cudaStream_t st);
+cudaError_t launch_batch_entries(const DevProblem *probs, const BatchTable &tb, WorkEntry *entries, cudaStream_t st);
+cudaError_t launch_batch_reduce(const DevProblem *probs, const BatchTable &tb, const TetOut *tout,
+                                const RasterOut *rout, cudaStream_t st);
 
 int sm_count();
 size_t partial_smem_bytes(int n_tets, int max_changed);

@@ -35,9 +35,12 @@ DEV_TIMEOUT = 0x20
 ENTRY_POINTS = (
     "morea_create_problem", "morea_destroy_problem", "morea_eval_full", "morea_eval_partial",
     "morea_commit_partial", "morea_check_folds", "morea_read_records", "morea_read_totals",
-    "morea_device_status", "morea_problem_info", "morea_profile", "morea_profile_read",
-    "morea_fold_magnitude_noalloc", "morea_status_string",
+    "morea_device_status", "morea_problem_info", "morea_batch_create", "morea_batch_destroy",
+    "morea_batch_eval_full", "morea_batch_capture", "morea_batch_replay", "morea_set_launch",
+    "morea_batch_set_launch", "morea_profile", "morea_profile_read", "morea_fold_magnitude_noalloc",
+    "morea_status_string",
 )
+MAX_BATCH = 64
 NOALLOC_MAX_TET_EVALS = 524288
 
 TET_RECORD_DTYPE = np.dtype([
@@ -93,6 +96,14 @@ def lib():
     L.morea_device_status.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_uint32)]
     L.morea_problem_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)]
+    pa = ctypes.POINTER(ctypes.c_void_p)
+    L.morea_batch_create.argtypes = [pa, i32, ctypes.POINTER(vp)]
+    L.morea_batch_destroy.argtypes = [vp]
+    L.morea_batch_eval_full.argtypes = [vp, ctypes.POINTER(i32), pa, pa, pa, pa, pa, vp]
+    L.morea_batch_capture.argtypes = [vp, ctypes.POINTER(i32), pa, pa, pa, pa, pa, vp]
+    L.morea_batch_replay.argtypes = [vp, vp]
+    L.morea_set_launch.argtypes = [vp, i32, i32]
+    L.morea_batch_set_launch.argtypes = [vp, i32, i32]
     L.morea_profile.argtypes = [vp, ctypes.c_uint32]
     L.morea_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                                      ctypes.POINTER(ctypes.c_int64)]
@@ -310,6 +321,10 @@ class Problem:
             _check(rc, "morea_device_status")
         return int(bits.value)
 
+    def set_launch(self, blocks_per_sm: int, chunk: int):
+        """Launch shape of the image/guidance passes (see morea_set_launch)."""
+        _check(self._L.morea_set_launch(self._h, int(blocks_per_sm), int(chunk)), "morea_set_launch")
+
     # -- instrumentation ----------------------------------------------------
     def profile(self, flags: int):
         """bit 0: time every launch of the hot kernel with CUDA events; bit 1: count voxel visits."""
@@ -320,6 +335,71 @@ class Problem:
         _check(self._L.morea_profile_read(self._h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(v)),
                "morea_profile_read")
         return ms.value, n.value, v.value
+
+
+class Batch:
+    """Several problems evaluated with one launch per kernel (morea_batch_*).
+
+    ``problems`` are :class:`Problem` objects with the same storage type and
+    modes; they must stay open while the batch lives.
+    """
+
+    def __init__(self, problems: Sequence[Problem]):
+        self.problems = list(problems)
+        arr = (ctypes.c_void_p * len(self.problems))(*[p.handle.value for p in self.problems])
+        h = ctypes.c_void_p()
+        _check(lib().morea_batch_create(arr, len(self.problems), ctypes.byref(h)), "morea_batch_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _check(lib().morea_batch_destroy(self._h), "morea_batch_destroy")
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _args(self, srcs, tgts, outs):
+        n = len(self.problems)
+        if len(srcs) != n or len(tgts) != n or len(outs) != n:
+            raise ValueError("one (src, tgt, out) per problem")
+        n_sol = (ctypes.c_int32 * n)(*[int(x.shape[0]) for x in srcs])
+        ptrs = lambda ts, dt, shp: (ctypes.c_void_p * n)(*[_dev(t, dt, shp(i), "batch tensor").value
+                                                        for i, t in enumerate(ts)])
+        V = [p.n_points for p in self.problems]
+        src_p = ptrs(srcs, torch.float32, lambda i: (n_sol[i], V[i], 3))
+        tgt_p = ptrs(tgts, torch.float32, lambda i: (n_sol[i], V[i], 3))
+        obj_p = ptrs([o[0] for o in outs], torch.float64, lambda i: (n_sol[i], 3))
+        fol_p = ptrs([o[1] for o in outs], torch.uint8, lambda i: (n_sol[i],))
+        sev_p = ptrs([o[2] for o in outs], torch.float64, lambda i: (n_sol[i],))
+        self._keep = (n_sol, src_p, tgt_p, obj_p, fol_p, sev_p)
+        return n_sol, src_p, tgt_p, obj_p, fol_p, sev_p
+
+    @staticmethod
+    def outputs(srcs):
+        return [(torch.empty((int(s.shape[0]), 3), dtype=torch.float64, device=s.device),
+                 torch.empty(int(s.shape[0]), dtype=torch.uint8, device=s.device),
+                 torch.empty(int(s.shape[0]), dtype=torch.float64, device=s.device)) for s in srcs]
+
+    def eval_full(self, srcs, tgts, outs=None, stream=None):
+        outs = outs if outs is not None else self.outputs(srcs)
+        _check(lib().morea_batch_eval_full(self._h, *self._args(srcs, tgts, outs), _stream(stream)),
+               "morea_batch_eval_full")
+        return outs
+
+    def capture(self, srcs, tgts, outs, stream):
+        """Record one batched evaluation of these (fixed) buffers into a CUDA graph."""
+        _check(lib().morea_batch_capture(self._h, *self._args(srcs, tgts, outs), _stream(stream)),
+               "morea_batch_capture")
+
+    def replay(self, stream=None):
+        _check(lib().morea_batch_replay(self._h, _stream(stream)), "morea_batch_replay")
+
+    def set_launch(self, blocks_per_sm: int, chunk: int):
+        _check(lib().morea_batch_set_launch(self._h, int(blocks_per_sm), int(chunk)), "morea_batch_set_launch")
 
 
 def fold_magnitude_noalloc(tets: torch.Tensor, ref_points: torch.Tensor, cdelta: torch.Tensor, shape_xyz,

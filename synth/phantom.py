@@ -384,7 +384,8 @@ C2_ELLIPSOIDS = [
 def make_c2(n_sol: int = 256, **kw) -> Problem:
     """256x256x160 float16 HU-like volumes (air -1000, soft tissue 0-80, bone
     700-1500), warp amplitude 6, graded 13x13x9 lattice (1521 points,
-    6912 tets, cell volumes spanning ~3 orders of magnitude), population 256."""
+    6912 tets, cell volumes spanning ~3 orders of magnitude), 300 guidance
+    pairs on six organ/bone contours, population 256."""
     rng = np.random.default_rng(4)
     flips = rng.integers(0, 2, size=3).astype(bool)
     xs = _graded_axis(256, 12, 1.25, flips[0])
@@ -408,7 +409,7 @@ def make_c2(n_sol: int = 256, **kw) -> Problem:
 
     args = dict(name="c2_256x256x160_f16", shape_xyz=(256, 256, 160), ellipsoids=C2_ELLIPSOIDS,
                 background=-1000.0, amp=6.0, noise_sigma=10.0, dtype="f16",
-                xs=xs, ys=ys, zs=zs, n_guid=1000, n_sol=n_sol, jitter=jit,
+                xs=xs, ys=ys, zs=zs, n_guid=300, n_sol=n_sol, jitter=jit,
                 tissue=[1.0, 1.0, 0.2, 0.8, 1.0, 10.0, 10.0, 10.0], seeds=(10, 11, 12),
                 groups=[1, 2, 3, 4, 5, 6])
     args.update(kw)

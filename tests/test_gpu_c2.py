@@ -1,0 +1,75 @@
+"""FP16 storage at full size: the 256x256x160 HU-like problem (graded mesh,
+6912 tets whose voxel counts span three orders of magnitude, population 256,
+coordinates up to the 65536 limit of the snapping grid).  The GPU evaluates
+the whole population; the FP64 oracle checks sampled solutions and partial
+requests.  Coverage and folds bit-exact, objectives within 1e-5 relative;
+the per-objective error against FP64 is printed (the FP16 error table)."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def c2():
+    from paper_2303_04873_gb300 import build
+    build.build()
+    from paper_2303_04873_gb300 import morea
+    p = synth.make_c2()
+    gp = morea.Problem(p, max_solutions=p.n_solutions, max_requests=p.n_solutions)
+    orc = oracle.Oracle(p, subvoxel_bits=gp.subvoxel_bits, trunc_radius=gp.trunc_radius)
+    return p, gp, orc
+
+
+def test_c2_full_population_sampled(c2):
+    p, gp, orc = c2
+    assert p.image_s.dtype == np.float16 and gp.subvoxel_bits == 8
+    src = torch.as_tensor(p.sol_src).cuda()
+    tgt = torch.as_tensor(p.sol_tgt).cuda()
+    obj, folded, sev = gp.eval_full(src, tgt)
+    obj = obj.cpu().numpy()
+    recs = gp.read_records(p.n_solutions)
+    tot = gp.read_totals(p.n_solutions)
+    assert (tot["n_vox"] == 2 * p.voxels()).all()
+    vox = recs["n_vox"].sum(axis=2)
+    assert vox.min() < 50 and vox.max() > 20000          # uneven tets
+    errs = []
+    for i in (0, 255):
+        r = orc.eval(p.sol_src[i], p.sol_tgt[i], with_tets=True)
+        np.testing.assert_array_equal(recs[i]["n_vox"], r["tets"]["n_vox"])
+        np.testing.assert_array_equal(recs[i]["folded"], r["tets"]["folded"])
+        assert int(folded[i]) == r["folded"]
+        rel = np.abs(obj[i] - r["obj"]) / np.abs(r["obj"])
+        errs.append(rel)
+        np.testing.assert_allclose(obj[i], r["obj"], rtol=1e-5, atol=0)
+    e = np.max(errs, axis=0)
+    print(f"\nFP16 storage, FP32 math vs FP64 oracle, max rel error: f_intensity {e[0]:.2e}, "
+          f"f_magnitude {e[1]:.2e}, f_guidance {e[2]:.2e}")
+
+
+def test_c2_partial_sampled(c2):
+    p, gp, orc = c2
+    src = torch.as_tensor(p.sol_src).cuda()
+    tgt = torch.as_tensor(p.sol_tgt).cuda()
+    gp.eval_full(src, tgt)
+    adj = synth.vertex_adjacency(p.tets, p.n_points)
+    rd = synth.partial_requests(p, adj, 1, 4, 32, 1.0, 7)[0]
+    dv = {k: torch.as_tensor(v).cuda() for k, v in rd.items()}
+    obj, folded, sev = gp.eval_partial(dv["slot"], dv["chg_off"], dv["chg_pts"], dv["chg_src"], dv["chg_tgt"])
+    obj = obj.cpu().numpy()
+    assert gp.device_status() == 0
+    off = rd["chg_off"]
+    for k in (3, 200):
+        ids = rd["chg_pts"][off[k]:off[k + 1]]
+        base = orc.eval(p.sol_src[k], p.sol_tgt[k])
+        ns, nt = p.sol_src[k].copy(), p.sol_tgt[k].copy()
+        ns[ids] = rd["chg_src"][off[k]:off[k + 1]]
+        nt[ids] = rd["chg_tgt"][off[k]:off[k + 1]]
+        r = orc.eval_partial(p.sol_src[k], p.sol_tgt[k], ns, nt, ids, base)
+        assert int(folded[k]) == r["folded"]
+        np.testing.assert_allclose(obj[k], r["obj"], rtol=1e-5, atol=0)
