@@ -263,6 +263,55 @@ morea_status morea_batch_replay(morea_batch *b, void *stream);
 morea_status morea_set_launch(morea_problem *p, int32_t blocks_per_sm, int32_t chunk);
 morea_status morea_batch_set_launch(morea_batch *b, int32_t blocks_per_sm, int32_t chunk);
 
+/* ---- surrogate pre-screen (a learned model; not part of the paper) ---- */
+
+/* Surrogate input of n_req candidate solutions: per vertex the displacement
+ * target - source (voxel units, snapped coordinates, [n_req][V][3] FP32,
+ * device) of the solution in slot[r] with the points of request r moved as in
+ * morea_eval_partial (chg_off/chg_pts/chg_src/chg_tgt, same layout; an empty
+ * request gives the committed solution).  An invalid slot gives NaN features
+ * and sets MOREA_DEV_BAD_SLOT. */
+morea_status morea_partial_features(morea_problem *p, int32_t n_req, const int32_t *slot,
+                                    const int32_t *chg_off, const int32_t *chg_pts, const float *chg_src,
+                                    const float *chg_tgt, float *out, void *stream);
+
+typedef struct morea_mlp morea_mlp;                     /* opaque handle */
+
+/* A 3-layer perceptron n_in -> h1 -> h2 -> n_out (ReLU, ReLU, linear) that
+ * predicts the (standardised) objectives of a solution from its displacement
+ * field, so that only the most promising offspring are evaluated exactly.
+ * Weights and activations are BF16 on the tensor cores with FP32
+ * accumulation; FP32 master weights and Adam moments are kept.  h1, h2
+ * multiples of 64, n_out <= 32, batches up to max_batch.  Parameters start at
+ * zero: set them with morea_mlp_set_params. */
+morea_status morea_mlp_create(int32_t n_in, int32_t h1, int32_t h2, int32_t n_out, int32_t max_batch,
+                              morea_mlp **out);
+morea_status morea_mlp_destroy(morea_mlp *n);
+
+/* Number of parameters and the padded input width kin (n_in rounded up to 64).
+ * Parameter vector layout (FP32): W1 [h1][kin] (columns >= n_in must be 0),
+ * b1 [h1], W2 [h2][h1], b2 [h2], W3 [n_out][h2], b3 [n_out]. */
+morea_status morea_mlp_info(const morea_mlp *n, int64_t *n_params, int32_t *padded_inputs);
+
+/* Copy the parameter vector in (resets the Adam state) / out.  host or device. */
+morea_status morea_mlp_set_params(morea_mlp *n, const float *params, void *stream);
+morea_status morea_mlp_get_params(morea_mlp *n, float *params, void *stream);
+
+/* y [batch][n_out] = network(x [batch][n_in]) (device FP32). */
+morea_status morea_mlp_forward(morea_mlp *n, int32_t batch, const float *x, float *y, void *stream);
+
+/* Gradient of the mean squared error between network(x) and t
+ * ([batch][n_out]) w.r.t. the parameter vector (grads, device FP32, may be
+ * NULL) and the loss (device scalar, may be NULL); no update. */
+morea_status morea_mlp_gradients(morea_mlp *n, int32_t batch, const float *x, const float *t, float *grads,
+                                 float *loss, void *stream);
+
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) on the mean squared error of
+ * (x, t) with learning rate lr; loss (device scalar, may be NULL) is the loss
+ * before the step. */
+morea_status morea_mlp_train_step(morea_mlp *n, int32_t batch, const float *x, const float *t, float lr,
+                                  float *loss, void *stream);
+
 /* Instrumentation for benchmarks (not a step of the method; the paper has no
  * counterpart).  flags bit 0: record a CUDA event pair on the call's stream
  * around every launch of the rasterisation/sampling kernel (the hot loop);

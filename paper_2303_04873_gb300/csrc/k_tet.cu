@@ -612,6 +612,48 @@ __global__ void __launch_bounds__(kBlock) k_band_rows(const uint8_t *__restrict_
     }
 }
 
+// Surrogate input of each partial candidate: per vertex the displacement
+// target - source (voxel units, snapped coordinates) of the slot's committed
+// solution with the request's moved points replaced.
+__global__ void __launch_bounds__(kBlock) k_partial_features(const DevProblem *__restrict__ dp,
+                                                            const int *__restrict__ slot,
+                                                            const int *__restrict__ chg_off,
+                                                            const int *__restrict__ chg_pts,
+                                                            const float *__restrict__ chg_src,
+                                                            const float *__restrict__ chg_tgt, float *out)
+{
+    const DevProblem &P = *dp;
+    const int r = blockIdx.x, V = P.n_points;
+    const int s = slot[r];
+    float *o = out + (size_t)r * V * 3;
+    const float inv_s = 1.0f / (float)P.S;
+    if (s < 0 || s >= P.max_sol) {
+        for (int v = threadIdx.x; v < 3 * V; v += kBlock) o[v] = __int_as_float(0x7fc00000);
+        if (threadIdx.x == 0) atomicOr(P.status, MOREA_DEV_BAD_SLOT);
+        return;
+    }
+    const int4 *sq = P.slot_q + (size_t)s * 2 * V;
+    for (int v = threadIdx.x; v < V; v += kBlock) {
+        const int4 a = sq[v], b = sq[V + v];
+        o[3 * v] = (float)(b.x - a.x) * inv_s;
+        o[3 * v + 1] = (float)(b.y - a.y) * inv_s;
+        o[3 * v + 2] = (float)(b.z - a.z) * inv_s;
+    }
+    __syncthreads();
+    const int a0 = chg_off[r], a1 = chg_off[r + 1];
+    for (int c = a0 + threadIdx.x; c < a1; c += kBlock) {
+        const int v = chg_pts[c];
+        if (v < 0 || v >= V) {
+            atomicOr(P.status, MOREA_DEV_BAD_POINT);
+            continue;
+        }
+        const int4 a = snap3(chg_src + 3 * (size_t)c, P), b = snap3(chg_tgt + 3 * (size_t)c, P);
+        o[3 * v] = (float)(b.x - a.x) * inv_s;
+        o[3 * v + 1] = (float)(b.y - a.y) * inv_s;
+        o[3 * v + 2] = (float)(b.z - a.z) * inv_s;
+    }
+}
+
 inline int grid_for(long long work, int block = kBlock)
 {
     long long b = (work + block - 1) / block;
@@ -760,6 +802,14 @@ cudaError_t launch_count_visits(const RasterOut *rout, const int *n_entries_dev,
                                 unsigned long long *visits, cudaStream_t st)
 {
     k_count_visits<<<sm_count() * 2, kBlock, 0, st>>>(rout, n_entries_dev, n_entries_host, visits);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_partial_features(const DevProblem *dp, int n_req, const int *slot, const int *chg_off,
+                                    const int *chg_pts, const float *chg_src, const float *chg_tgt, float *out,
+                                    cudaStream_t st)
+{
+    k_partial_features<<<n_req, kBlock, 0, st>>>(dp, slot, chg_off, chg_pts, chg_src, chg_tgt, out);
     return cudaGetLastError();
 }
 

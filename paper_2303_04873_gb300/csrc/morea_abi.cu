@@ -502,6 +502,16 @@ morea_status morea_read_totals(morea_problem *p, int32_t n_sol, const int32_t *s
     return from_cuda(launch_gather_totals(p->hp, n_sol, slot, out, (cudaStream_t)stream));
 }
 
+morea_status morea_partial_features(morea_problem *p, int32_t n_req, const int32_t *slot, const int32_t *chg_off,
+                                    const int32_t *chg_pts, const float *chg_src, const float *chg_tgt, float *out,
+                                    void *stream)
+{
+    if (!p || n_req < 1 || !slot || !chg_off || !out) return MOREA_EINVAL;
+    DeviceGuard g(p->device);
+    return from_cuda(launch_partial_features(p->dp, n_req, slot, chg_off, chg_pts, chg_src, chg_tgt, out,
+                                             (cudaStream_t)stream));
+}
+
 morea_status morea_device_status(morea_problem *p, void *stream, uint32_t *bits)
 {
     if (!p) return MOREA_EINVAL;

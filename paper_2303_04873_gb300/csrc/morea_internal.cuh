@@ -177,6 +177,10 @@ cudaError_t launch_batch_entries(const DevProblem *probs, const BatchTable &tb, 
 cudaError_t launch_batch_reduce(const DevProblem *probs, const BatchTable &tb, const TetOut *tout,
                                 const RasterOut *rout, cudaStream_t st);
 
+cudaError_t launch_partial_features(const DevProblem *dp, int n_req, const int *slot, const int *chg_off,
+                                    const int *chg_pts, const float *chg_src, const float *chg_tgt, float *out,
+                                    cudaStream_t st);
+
 int sm_count();
 size_t partial_smem_bytes(int n_tets, int max_changed);
 

@@ -35,6 +35,9 @@ DEV_TIMEOUT = 0x20
 ENTRY_POINTS = (
     "morea_create_problem", "morea_destroy_problem", "morea_eval_full", "morea_eval_partial",
     "morea_commit_partial", "morea_check_folds", "morea_read_records", "morea_read_totals",
+    "morea_partial_features", "morea_mlp_create", "morea_mlp_destroy", "morea_mlp_info",
+    "morea_mlp_set_params", "morea_mlp_get_params", "morea_mlp_forward", "morea_mlp_gradients",
+    "morea_mlp_train_step",
     "morea_device_status", "morea_problem_info", "morea_batch_create", "morea_batch_destroy",
     "morea_batch_eval_full", "morea_batch_capture", "morea_batch_replay", "morea_set_launch",
     "morea_batch_set_launch", "morea_profile", "morea_profile_read", "morea_fold_magnitude_noalloc",
@@ -96,6 +99,15 @@ def lib():
     L.morea_device_status.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_uint32)]
     L.morea_problem_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)]
+    L.morea_partial_features.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp]
+    L.morea_mlp_create.argtypes = [i32, i32, i32, i32, i32, ctypes.POINTER(vp)]
+    L.morea_mlp_destroy.argtypes = [vp]
+    L.morea_mlp_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(i32)]
+    L.morea_mlp_set_params.argtypes = [vp, vp, vp]
+    L.morea_mlp_get_params.argtypes = [vp, vp, vp]
+    L.morea_mlp_forward.argtypes = [vp, i32, vp, vp, vp]
+    L.morea_mlp_gradients.argtypes = [vp, i32, vp, vp, vp, vp, vp]
+    L.morea_mlp_train_step.argtypes = [vp, i32, vp, vp, ctypes.c_float, vp, vp]
     pa = ctypes.POINTER(ctypes.c_void_p)
     L.morea_batch_create.argtypes = [pa, i32, ctypes.POINTER(vp)]
     L.morea_batch_destroy.argtypes = [vp]
@@ -321,6 +333,21 @@ class Problem:
             _check(rc, "morea_device_status")
         return int(bits.value)
 
+    def partial_features(self, slots: torch.Tensor, chg_off: torch.Tensor, chg_pts: torch.Tensor,
+                         chg_src: torch.Tensor, chg_tgt: torch.Tensor, out: Optional[torch.Tensor] = None,
+                         stream=None) -> torch.Tensor:
+        """Displacement features [n][V*3] of the candidates of a partial-request list."""
+        n = int(slots.shape[0])
+        c = int(chg_pts.shape[0])
+        if out is None:
+            out = torch.empty((n, self.n_points * 3), dtype=torch.float32, device=slots.device)
+        _check(self._L.morea_partial_features(
+            self._h, n, _dev(slots, torch.int32, (n,), "slots"), _dev(chg_off, torch.int32, (n + 1,), "chg_off"),
+            _dev(chg_pts, torch.int32, (c,), "chg_pts"), _dev(chg_src, torch.float32, (c, 3), "chg_src"),
+            _dev(chg_tgt, torch.float32, (c, 3), "chg_tgt"), _dev(out, torch.float32, (n, self.n_points * 3), "out"),
+            _stream(stream)), "morea_partial_features")
+        return out
+
     def set_launch(self, blocks_per_sm: int, chunk: int):
         """Launch shape of the image/guidance passes (see morea_set_launch)."""
         _check(self._L.morea_set_launch(self._h, int(blocks_per_sm), int(chunk)), "morea_set_launch")
@@ -400,6 +427,96 @@ class Batch:
 
     def set_launch(self, blocks_per_sm: int, chunk: int):
         _check(lib().morea_batch_set_launch(self._h, int(blocks_per_sm), int(chunk)), "morea_batch_set_launch")
+
+
+class Mlp:
+    """The surrogate network n_in -> h1 -> h2 -> n_out (morea_mlp_*)."""
+
+    def __init__(self, n_in: int, h1: int = 512, h2: int = 256, n_out: int = 3, max_batch: int = 1024,
+                 seed: Optional[int] = 0):
+        self.n_in, self.h1, self.h2, self.n_out, self.max_batch = n_in, h1, h2, n_out, max_batch
+        h = ctypes.c_void_p()
+        _check(lib().morea_mlp_create(n_in, h1, h2, n_out, max_batch, ctypes.byref(h)), "morea_mlp_create")
+        self._h = h
+        npar, kin = ctypes.c_int64(), ctypes.c_int32()
+        _check(lib().morea_mlp_info(h, ctypes.byref(npar), ctypes.byref(kin)), "morea_mlp_info")
+        self.n_params, self.kin = npar.value, kin.value
+        self._loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+        if seed is not None:
+            self.set_params(self.init_params(seed))
+
+    def init_params(self, seed: int) -> np.ndarray:
+        """He-uniform weights, zero biases, in the library's parameter layout."""
+        rng = np.random.default_rng(seed)
+        def he(rows, cols):
+            b = np.sqrt(6.0 / cols)
+            return rng.uniform(-b, b, size=(rows, cols))
+        W1 = np.zeros((self.h1, self.kin))
+        W1[:, :self.n_in] = he(self.h1, self.n_in)
+        parts = [W1.ravel(), np.zeros(self.h1), he(self.h2, self.h1).ravel(), np.zeros(self.h2),
+                 he(self.n_out, self.h2).ravel(), np.zeros(self.n_out)]
+        return np.concatenate(parts).astype(np.float32)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _check(lib().morea_mlp_destroy(self._h), "morea_mlp_destroy")
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params):
+        if isinstance(params, torch.Tensor):
+            t = params.to(torch.float32).contiguous()
+            _check(lib().morea_mlp_set_params(self._h, ctypes.c_void_p(t.data_ptr()), _stream(None)),
+                   "morea_mlp_set_params")
+            torch.cuda.current_stream().synchronize()
+            return
+        a = np.ascontiguousarray(params, dtype=np.float32)
+        if a.size != self.n_params:
+            raise ValueError(f"expected {self.n_params} parameters")
+        _check(lib().morea_mlp_set_params(self._h, a.ctypes.data_as(ctypes.c_void_p), _stream(None)),
+               "morea_mlp_set_params")
+        torch.cuda.current_stream().synchronize()
+
+    def get_params(self) -> np.ndarray:
+        out = torch.empty(self.n_params, dtype=torch.float32, device="cuda")
+        _check(lib().morea_mlp_get_params(self._h, ctypes.c_void_p(out.data_ptr()), _stream(None)),
+               "morea_mlp_get_params")
+        return out.cpu().numpy()
+
+    def forward(self, x: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        """Predictions for x [n][n_in] (n may exceed max_batch; processed in chunks)."""
+        n = int(x.shape[0])
+        if out is None:
+            out = torch.empty((n, self.n_out), dtype=torch.float32, device=x.device)
+        _dev(x, torch.float32, (n, self.n_in), "x")
+        for a in range(0, n, self.max_batch):
+            b = min(n, a + self.max_batch)
+            _check(lib().morea_mlp_forward(self._h, b - a, ctypes.c_void_p(x[a:b].data_ptr()),
+                                           ctypes.c_void_p(out[a:b].data_ptr()), _stream(stream)),
+                   "morea_mlp_forward")
+        return out
+
+    def gradients(self, x: torch.Tensor, t: torch.Tensor, stream=None):
+        n = int(x.shape[0])
+        g = torch.empty(self.n_params, dtype=torch.float32, device=x.device)
+        _check(lib().morea_mlp_gradients(self._h, n, _dev(x, torch.float32, (n, self.n_in), "x"),
+                                         _dev(t, torch.float32, (n, self.n_out), "t"), ctypes.c_void_p(g.data_ptr()),
+                                         ctypes.c_void_p(self._loss.data_ptr()), _stream(stream)),
+               "morea_mlp_gradients")
+        return g, self._loss
+
+    def train_step(self, x: torch.Tensor, t: torch.Tensor, lr: float, stream=None) -> torch.Tensor:
+        n = int(x.shape[0])
+        _check(lib().morea_mlp_train_step(self._h, n, _dev(x, torch.float32, (n, self.n_in), "x"),
+                                          _dev(t, torch.float32, (n, self.n_out), "t"), float(lr),
+                                          ctypes.c_void_p(self._loss.data_ptr()), _stream(stream)),
+               "morea_mlp_train_step")
+        return self._loss
 
 
 def fold_magnitude_noalloc(tets: torch.Tensor, ref_points: torch.Tensor, cdelta: torch.Tensor, shape_xyz,

@@ -1,0 +1,64 @@
+"""Host logic of the optimiser: exact hypervolume against brute-force cell
+counting, Pareto filtering and the archive's acceptance rule (Sec. 3)."""
+
+import itertools
+
+import numpy as np
+import pytest
+
+from paper_2303_04873_gb300 import ea
+
+
+def brute_hv(points, ref):
+    pts = np.asarray(points, float)
+    coords = [np.unique(np.concatenate([pts[:, a][pts[:, a] < ref[a]], [ref[a]]])) for a in range(3)]
+    vol = 0.0
+    for i, j, k in itertools.product(*(range(len(c) - 1) for c in coords)):
+        lo = np.array([coords[0][i], coords[1][j], coords[2][k]])
+        hi = np.array([coords[0][i + 1], coords[1][j + 1], coords[2][k + 1]])
+        if np.any(np.all(pts <= lo, axis=1)):
+            vol += np.prod(hi - lo)
+    return vol
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_hv3d_matches_cell_counting(seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(1, 13))
+    pts = rng.integers(0, 6, size=(n, 3)).astype(float)       # ties and duplicates
+    pts[0] = [7.0, 1.0, 1.0]                                    # outside the box in x
+    ref = np.array([6.5, 6.0, 5.5])
+    assert ea.hv3d(pts, ref) == pytest.approx(brute_hv(pts, ref), rel=1e-12, abs=1e-12)
+
+
+def test_hv_closed_forms():
+    assert ea.hv3d(np.array([[1.0, 2.0, 3.0]]), [4.0, 4.0, 4.0]) == pytest.approx(3 * 2 * 1)
+    assert ea.hv2d(np.array([[0.0, 2.0], [1.0, 1.0]]), [3.0, 3.0]) == pytest.approx(3 * 1 + 2 * 1)
+    assert ea.hv3d(np.zeros((0, 3)), [1, 1, 1]) == 0.0
+
+
+def test_nondominated_and_archive():
+    pts = np.array([[1, 2, 3], [2, 1, 3], [2, 2, 3], [1, 2, 3], [0, 5, 5]], float)
+    nd = ea.nondominated(pts)
+    assert {tuple(r) for r in nd} == {(1, 2, 3), (2, 1, 3), (0, 5, 5)}
+    arc = ea.Archive()
+    for p in pts:
+        arc.add(p)
+    assert {tuple(r) for r in arc.pts} == {(1, 2, 3), (2, 1, 3), (0, 5, 5)}
+    assert not arc.accepts(np.array([1.0, 2.0, 3.0]))          # duplicate
+    assert not arc.accepts(np.array([3.0, 3.0, 3.0]))          # dominated
+    assert arc.accepts(np.array([0.5, 3.0, 3.0]))              # non-dominated
+    assert ea.dominates(np.array([1, 1, 1]), np.array([1, 2, 1]))
+    assert not ea.dominates(np.array([1, 1, 1]), np.array([1, 1, 1]))
+
+
+def test_bfs_orders_are_connected_neighbourhoods():
+    import synth
+    p = synth.make_c0(n_sol=1)
+    orders = ea.bfs_orders(p.tets, p.n_points, 12)
+    adj = synth.vertex_adjacency(p.tets, p.n_points)
+    for v in (0, 31, 62, 124):
+        o = orders[v]
+        assert o[0] == v and len(set(o)) == 12
+        for k in range(1, 12):                                # each vertex touches an earlier one
+            assert any(int(u) in adj[int(o[k])] for u in o[:k])
