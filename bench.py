@@ -547,6 +547,8 @@ def run_surrogate_ea(args):
     plain = ea.run(gp, p, G, R, seed=200, step_scale=step, orders=orders, hv_every=10)
     sur = ea.run(gp, p, G, R, seed=200, step_scale=step, orders=orders, hv_every=10, surrogate=tr["surrogate"],
                  ref=plain["ref"])
+    rnd = ea.run(gp, p, G, R, seed=200, step_scale=step, orders=orders, hv_every=10, random_screen=True,
+                 ref=plain["ref"])
     # the plain run's hypervolume when it had used as many exact evaluations as the screened run
     hx = np.array([h[1] for h in plain["history"]], float)
     hv = np.array([h[2] for h in plain["history"]], float)
@@ -561,6 +563,7 @@ def run_surrogate_ea(args):
                    "training_samples": n_samples, "epochs": args.epochs, "train_seconds": t_train},
         "hv_plain": plain["hv"], "hv_surrogate": sur["hv"], "hv_ratio": sur["hv"] / plain["hv"],
         "hv_plain_at_surrogate_budget": hv_plain_same_budget,
+        "hv_random_screen": rnd["hv"], "exact_random_screen": rnd["exact"],
         "exact_plain": plain["exact"], "exact_surrogate": sur["exact"],
         "surrogate_mae": tr["mae"].tolist(), "surrogate_r2": tr["r2"].tolist(),
         "history_plain": plain["history"], "history_surrogate": sur["history"],

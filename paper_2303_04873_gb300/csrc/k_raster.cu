@@ -37,6 +37,22 @@ struct QuadOf<__half> {
     using T = uint2;
 };
 
+// Loads of per-item constants where they are used (volatile, so they are not
+// hoisted into registers that would stay live across the whole item).
+__device__ __forceinline__ float4 ld_volatile_f4(const unsigned char *p)
+{
+    float4 v;
+    asm volatile("ld.global.nc.v4.f32 {%0,%1,%2,%3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ float2 ld_volatile_f2(const unsigned char *p)
+{
+    float2 v;
+    asm volatile("ld.global.nc.v2.f32 {%0,%1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+    return v;
+}
+
 __device__ __forceinline__ float ld_img(const float *p, int idx) { return __ldg(p + idx); }
 __device__ __forceinline__ float ld_img(const __half *p, int idx) { return __half2float(__ldg(p + idx)); }
 
@@ -236,7 +252,7 @@ __device__ __forceinline__ void guidance_voxel(const DevProblem &P, int side, in
 // Pair-transfer guidance of one tet copy: the guidance points of this side
 // located in the copy (exact perturbed inside test on their snapped
 // coordinates), mapped and compared with their partners.
-__device__ __forceinline__ void guidance_pairs(const DevProblem &P, const RasterSetup *su, int side, int lane,
+__device__ __noinline__ void guidance_pairs(const DevProblem &P, const RasterSetup *su, int side, int lane,
                                             float &s_g, float &c_g, int &ngp)
 {
     const int cs = P.cshift, kb = P.kbits;
@@ -313,6 +329,22 @@ __device__ __forceinline__ int2 pack_band_row(int lo, int hi, int j, int k)
     return make_int2(lo | (hi << 16), j | (k << 16));
 }
 
+// Per-warp queue of the rows found by the row phase.  Voxels of successive
+// rows form one stream (index u); a row occupies [start, next row's start),
+// its voxel x = d + u, its image row starts at linear index base, and
+// (rx, ry, rz) holds the row's part of the affine map, so a voxel's mapped
+// position is fma(M[a][0], x - s0x, r_a): the same FMA chain as evaluating the
+// map from scratch.  Rows accumulate across row batches and the voxels are
+// processed in full windows of 32 (one voxel per lane, coalesced along rows).
+constexpr int kRowQ = 128;              // ring capacity (rows); power of two
+constexpr int kWin = 32;                // voxels per window (one per lane)
+struct RowQueue {
+    int start[kRowQ];
+    int d[kRowQ];
+    int base[kRowQ];
+    float rx[kRowQ], ry[kRowQ], rz[kRowQ];
+};
+
 // Image pass (a4, a5, a7): one warp per (entry, side).
 template <typename TI, int HMODE, int PASS>
 __global__ void __launch_bounds__(kBlock, 4) k_raster(const DevProblem *__restrict__ probs,
@@ -323,7 +355,10 @@ __global__ void __launch_bounds__(kBlock, 4) k_raster(const DevProblem *__restri
                                                      int *queue)
 {
     using QT = typename QuadOf<TI>::T;
+    __shared__ RowQueue rowq[kBlock / 32];
     const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    RowQueue &Q = rowq[threadIdx.x >> 5];
     const int n_ent = n_entries_dev ? min(*n_entries_dev, n_entries_host) : n_entries_host;
     const int n_items = 2 * n_ent;
     run_items(n_items, chunk, queue, [&](const int item) {
@@ -331,14 +366,9 @@ __global__ void __launch_bounds__(kBlock, 4) k_raster(const DevProblem *__restri
         const int e = item - side * n_ent;
         const RasterSetup *su = setup + 2 * (size_t)e + side;
         const unsigned char *sb = reinterpret_cast<const unsigned char *>(su);
-        const float4 m0 = __ldg(reinterpret_cast<const float4 *>(sb + offsetof(RasterSetup, M)));
-        const float4 m1 = __ldg(reinterpret_cast<const float4 *>(sb + offsetof(RasterSetup, M) + 16));
-        const float4 m2 = __ldg(reinterpret_cast<const float4 *>(sb + offsetof(RasterSetup, M) + 32));
-        const float4 t4 = __ldg(reinterpret_cast<const float4 *>(sb + offsetof(RasterSetup, t0)));
         const int4 bx = __ldg(reinterpret_cast<const int4 *>(sb + offsetof(RasterSetup, ilo)));
         const int2 bz2 = __ldg(reinterpret_cast<const int2 *>(sb + offsetof(RasterSetup, klo)));
-        const int valid = __float_as_int(t4.w);
-        // M = (m0.x m0.y m0.z; m0.w m1.x m1.y; m1.z m1.w m2.x), s0 = m2.yzw, t0 = t4.xyz
+        const int valid = __ldg(reinterpret_cast<const int *>(sb + offsetof(RasterSetup, valid)));
         float s_img = 0.0f, c_img = 0.0f, s_g = 0.0f, c_g = 0.0f;
         int nvox = 0, ngp = 0;
         int nband = 0;                                // band rows recorded (warp-uniform)
@@ -352,6 +382,54 @@ __global__ void __launch_bounds__(kBlock, 4) k_raster(const DevProblem *__restri
             const int nyb = max(bx.w - jlo + 1, 1), nzb = bz2.y - klo + 1;
             const int n_rows = (ilo <= ihi && bx.w >= jlo && nzb > 0) ? nyb * nzb : 0;
             const bool inner = (valid & 2) != 0;
+            // row queue state (warp-uniform): live rows [head, tail), voxel
+            // stream [pend, total) not yet processed
+            int head = 0, tail = 0, pend = 0, total = 0;
+            auto voxel = [&](int u, int d, int base, float rx, float ry, float rz, float M00, float M10, float M20,
+                             float s0x) {
+                const int x = d + u;
+                const float a = ld_img(own, base + x);
+                const float dx = (float)x - s0x;
+                const float yx = fmaf(M00, dx, rx);
+                const float yy = fmaf(M10, dx, ry);
+                const float yz = fmaf(M20, dx, rz);
+                const float b = inner ? trilin_quad_inner(oq, nx, ny, yx, yy, yz)
+                                      : trilin_quad(oq, nx, ny, nz, yx, yy, yz);
+                kadd(s_img, c_img, hfun<HMODE>(a, b));
+            };
+            // voxels [wbase, wbase + w) of the stream, one per lane.  The row of
+            // the window's first voxel is `head`; the later rows that start
+            // inside the window set bit (start - wbase) of `starts`, so a
+            // lane's row is head + popc(starts & bits <= its position).
+            auto window = [&](int wbase, int w) {
+                const int r = head + 1 + lane;
+                unsigned bit = 0u;
+                if (r < tail) {
+                    const int st = Q.start[r & (kRowQ - 1)];
+                    if (st < wbase + 32) bit = 1u << (st - wbase);
+                }
+                const unsigned starts = __reduce_or_sync(FULL, bit);
+                const unsigned upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
+                const int q = (head + __popc(starts & upto)) & (kRowQ - 1);
+                if (lane < w) {
+                    // first column of M and s0.x: a.x, a.w, b.z, c.y
+                    const float4 ma = ld_volatile_f4(sb + offsetof(RasterSetup, M));
+                    const float2 mbz = ld_volatile_f2(sb + offsetof(RasterSetup, M) + 24);
+                    const float2 mcy = ld_volatile_f2(sb + offsetof(RasterSetup, M) + 32);
+                    voxel(wbase + lane, Q.d[q], Q.base[q], Q.rx[q], Q.ry[q], Q.rz[q], ma.x, ma.w, mbz.x, mcy.y);
+                }
+                __syncwarp();
+            };
+            // drop rows whose voxels all precede pend
+            auto advance = [&]() {
+                for (;;) {
+                    const int i = head + 1 + lane;
+                    const bool done = i < tail && Q.start[i & (kRowQ - 1)] <= pend;
+                    const unsigned bm = __ballot_sync(FULL, done);
+                    head += __popc(bm);
+                    if (bm != FULL) break;
+                }
+            };
             // lane -> row (jlo + dj, klo + dk); rows advance by 32 per batch
             int dk = lane / nyb, dj = lane - dk * nyb;
             const int inc_k = 32 / nyb, inc_j = 32 - inc_k * nyb;
@@ -388,35 +466,37 @@ __global__ void __launch_bounds__(kBlock, 4) k_raster(const DevProblem *__restri
                     const int v = __shfl_up_sync(FULL, incl, o);
                     if (lane >= o) incl += v;
                 }
-                const int total = __shfl_sync(FULL, incl, 31);
-                nvox += total;
-                const int d = lo - (incl - cnt);          // x = d + v for the row's voxels
-                const int jk = j | (k << 16);
-                for (int vb = 0; vb < total; vb += 32) {
-                    const int v = vb + lane;
-                    int ow = 0;
-#pragma unroll
-                    for (int step = 16; step >= 1; step >>= 1) {
-                        const int p = __shfl_sync(FULL, incl, ow + step - 1);
-                        if (p <= v) ow += step;
-                    }
-                    const int od = __shfl_sync(FULL, d, ow);
-                    const int ojk = __shfl_sync(FULL, jk, ow);
-                    if (v < total) {
-                        const int x = od + v;
-                        const int oj = ojk & 0xffff, okk = ojk >> 16;
-                        const int idx = (okk * ny + oj) * nx + x;
-                        const float a = ld_img(own, idx);
-                        const float dx = (float)x - m2.y, dy = (float)oj - m2.z, dz = (float)okk - m2.w;
-                        const float yx = fmaf(m0.x, dx, fmaf(m0.y, dy, fmaf(m0.z, dz, t4.x)));
-                        const float yy = fmaf(m0.w, dx, fmaf(m1.x, dy, fmaf(m1.y, dz, t4.y)));
-                        const float yz = fmaf(m1.z, dx, fmaf(m1.w, dy, fmaf(m2.x, dz, t4.z)));
-                        const float b = inner ? trilin_quad_inner(oq, nx, ny, yx, yy, yz)
-                                              : trilin_quad(oq, nx, ny, nz, yx, yy, yz);
-                        kadd(s_img, c_img, hfun<HMODE>(a, b));
-                    }
+                const int batch_total = __shfl_sync(FULL, incl, 31);
+                nvox += batch_total;
+                // append the non-empty rows to the queue
+                const unsigned ne = __ballot_sync(FULL, cnt > 0);
+                if (cnt > 0) {
+                    // M = (a.x a.y a.z; a.w b.x b.y; b.z b.w c.x), s0 = c.yzw, t0 = t.xyz
+                    const float4 ma = ld_volatile_f4(sb + offsetof(RasterSetup, M));
+                    const float4 mb = ld_volatile_f4(sb + offsetof(RasterSetup, M) + 16);
+                    const float4 mc = ld_volatile_f4(sb + offsetof(RasterSetup, M) + 32);
+                    const float4 mt = ld_volatile_f4(sb + offsetof(RasterSetup, t0));
+                    const int q = (tail + __popc(ne & lt_mask)) & (kRowQ - 1);
+                    const int st = total + incl - cnt;
+                    const float dy = (float)j - mc.z, dz = (float)k - mc.w;
+                    Q.start[q] = st;
+                    Q.d[q] = lo - st;
+                    Q.base[q] = (k * ny + j) * nx;
+                    Q.rx[q] = fmaf(ma.y, dy, fmaf(ma.z, dz, mt.x));
+                    Q.ry[q] = fmaf(mb.x, dy, fmaf(mb.y, dz, mt.y));
+                    Q.rz[q] = fmaf(mb.w, dy, fmaf(mc.x, dz, mt.z));
+                }
+                tail += __popc(ne);
+                total += batch_total;
+                __syncwarp();
+                while (total - pend >= kWin) {
+                    window(pend, kWin);
+                    pend += kWin;
+                    advance();
                 }
             }
+            if (total > pend) window(pend, total - pend);
+            __syncwarp();
             if (PASS == kPassImagePairs && P.n_guid > 0) guidance_pairs(P, su, side, lane, s_g, c_g, ngp);
         }
         const float e_img = warp_comp_sum(s_img, -c_img);
