@@ -1,11 +1,12 @@
 // The hot loop of libmorea (steps a4-a7): for each (work entry, side) one
-// warp walks the voxel-centre rows of the tet copy's bounding box, solves the
-// exact integer x-interval of each row, spreads the row's voxels over the
-// 32 lanes, maps every voxel centre p into the other image with the tet's
+// warp walks the voxel-centre rows that can meet the tet copy (per z-slice,
+// the y-extent of its cross-section), solves the exact integer x-interval of
+// each row, queues the rows' voxels and processes them 32 at a time, one per
+// lane: it maps every voxel centre p into the other image with the tet's
 // affine map, samples the other image trilinearly, accumulates h (Sec. 4.1.2)
-// and the continuous guidance term (Sec. 4.1.3) in compensated FP32, and
-// reduces the per-lane sums with warp shuffles into one record per
-// (entry, side).
+// in compensated FP32, and reduces the per-lane sums with warp shuffles into
+// one record per (entry, side).  The continuous guidance term (Sec. 4.1.3)
+// is summed by k_guidance over the rows this pass records.
 //
 // Voxel association (exact): a voxel centre P is inside the copy iff for
 // every face f: A_f i + B_f(j, k) > 0 (integers, simulation-of-simplicity tie
@@ -16,8 +17,7 @@
 // Memory traffic per voxel visit: the own voxel (one 4- or 2-byte load), one
 // 16- or 8-byte load per z-plane of the other image's 2x2x2 neighbourhood
 // from its "quad" copy, and the band mask only in rows that touch a guidance
-// band.  Rows are distributed to lanes by a warp scan; each lane finds the
-// row of its voxel by a 5-step shuffle search.
+// band.
 #include "morea_device.cuh"
 
 namespace morea {
@@ -229,6 +229,35 @@ __device__ __forceinline__ void row_interval(const FaceRow *__restrict__ f, int 
     }
 }
 
+// y-extent [y0, y1] (snapped units) of the cross-section of a tet copy with
+// the plane z = zq: the intersections of its six edges with the plane.  The
+// vertices are integers below 2^17, so each intersection is within 2^-6 of
+// its exact value (one rounded division and one FMA); callers widen the
+// extent by more than that.  Empty (y0 > y1) if no edge meets the plane.
+__device__ __forceinline__ void slice_y_extent(const int4 *vq, float zq, float &y0, float &y1)
+{
+    float y[4], z[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const int4 t = __ldg(vq + v);
+        y[v] = (float)t.y;
+        z[v] = (float)t.z;
+    }
+    y0 = INFINITY;
+    y1 = -INFINITY;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = a + 1; b < 4; ++b) {
+            if (fminf(z[a], z[b]) <= zq && zq <= fmaxf(z[a], z[b])) {
+                float ya = y[a], yb = y[b];
+                if (z[a] != z[b]) ya = yb = fmaf((zq - z[a]) / (z[b] - z[a]), y[b] - y[a], y[a]);
+                y0 = fminf(y0, fminf(ya, yb));
+                y1 = fmaxf(y1, fmaxf(ya, yb));
+            }
+        }
+}
+
 // Continuous guidance term of one voxel that lies in at least one band.
 __device__ __forceinline__ void guidance_voxel(const DevProblem &P, int side, int idx, float yx, float yy, float yz,
                                             float &s_g, float &c_g)
@@ -430,69 +459,97 @@ __global__ void __launch_bounds__(kBlock, 4) k_raster(const DevProblem *__restri
                     if (bm != FULL) break;
                 }
             };
-            // lane -> row (jlo + dj, klo + dk); rows advance by 32 per batch
-            int dk = lane / nyb, dj = lane - dk * nyb;
-            const int inc_k = 32 / nyb, inc_j = 32 - inc_k * nyb;
-            for (int rb = 0; rb < n_rows; rb += 32) {
-                int lo = 1, hi = 0;
-                const int j = jlo + dj, k = klo + dk;
-                if (dk < nzb) row_interval(su->f, dj, dk, ilo, ihi, lo, hi);
-                if (PASS == kPassImageBand) {
-                    // record the band part of each row (warp-aggregated append)
-                    int blo = 1, bhi = 0;
-                    if (dk < nzb && hi >= lo) {
-                        const short2 br = __ldg(P.bandrow[side] + (k * ny + j));
-                        blo = max(lo, (int)br.x);
-                        bhi = min(hi, (int)br.y);
-                    }
-                    const bool band = blo <= bhi;
-                    const unsigned bm = __ballot_sync(FULL, band);
-                    if (bm) {
-                        const int pos = nband + __popc(bm & ((1u << lane) - 1u));
-                        if (band && pos < kBandRows) brec[pos] = pack_band_row(blo, bhi, j, k);
-                        nband += __popc(bm);
+            // Rows of the bounding box that can meet the copy, 32 z-slices at
+            // a time: lane l finds the y-extent [jl, jl + ns) of slice
+            // klo + kc + l, a warp scan numbers the rows of the chunk, and the
+            // row of lane l in batch rb is found by a binary search over the
+            // scan.  row_interval stays the exact test of every row.
+            const float Sf = (float)P.S, Hf = (float)P.H;
+            for (int kc = 0; kc < nzb && n_rows > 0; kc += 32) {
+                int jl = 0, ns = 0;
+                if (kc + lane < nzb) {
+                    float y0, y1;
+                    slice_y_extent(entries[e].q[side], (float)(klo + kc + lane) * Sf + Hf, y0, y1);
+                    if (y0 <= y1) {
+                        const float m = Sf * 0.0625f + 1.0f;   // 1/16 voxel + 1 unit
+                        jl = max(jlo, (int)ceilf((y0 - m - Hf) / Sf));
+                        ns = max(0, min(bx.w, (int)floorf((y1 + m - Hf) / Sf)) - jl + 1);
                     }
                 }
-                dj += inc_j;
-                dk += inc_k;
-                if (dj >= nyb) {
-                    dj -= nyb;
-                    dk += 1;
-                }
-                const int cnt = max(0, hi - lo + 1);
-                int incl = cnt;
+                int srow = ns;                            // inclusive scan of the slices' row counts
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
-                    const int v = __shfl_up_sync(FULL, incl, o);
-                    if (lane >= o) incl += v;
+                    const int v = __shfl_up_sync(FULL, srow, o);
+                    if (lane >= o) srow += v;
                 }
-                const int batch_total = __shfl_sync(FULL, incl, 31);
-                nvox += batch_total;
-                // append the non-empty rows to the queue
-                const unsigned ne = __ballot_sync(FULL, cnt > 0);
-                if (cnt > 0) {
-                    // M = (a.x a.y a.z; a.w b.x b.y; b.z b.w c.x), s0 = c.yzw, t0 = t.xyz
-                    const float4 ma = ld_volatile_f4(sb + offsetof(RasterSetup, M));
-                    const float4 mb = ld_volatile_f4(sb + offsetof(RasterSetup, M) + 16);
-                    const float4 mc = ld_volatile_f4(sb + offsetof(RasterSetup, M) + 32);
-                    const float4 mt = ld_volatile_f4(sb + offsetof(RasterSetup, t0));
-                    const int q = (tail + __popc(ne & lt_mask)) & (kRowQ - 1);
-                    const int st = total + incl - cnt;
-                    const float dy = (float)j - mc.z, dz = (float)k - mc.w;
-                    Q.start[q] = st;
-                    Q.d[q] = lo - st;
-                    Q.base[q] = (k * ny + j) * nx;
-                    Q.rx[q] = fmaf(ma.y, dy, fmaf(ma.z, dz, mt.x));
-                    Q.ry[q] = fmaf(mb.x, dy, fmaf(mb.y, dz, mt.y));
-                    Q.rz[q] = fmaf(mb.w, dy, fmaf(mc.x, dz, mt.z));
-                }
-                tail += __popc(ne);
-                total += batch_total;
-                __syncwarp();
-                while (total - pend >= kWin) {
-                    window(pend, kWin);
-                    pend += kWin;
-                    advance();
+                const int chunk_rows = __shfl_sync(FULL, srow, 31);
+                for (int rb = 0; rb < chunk_rows; rb += 32) {
+                    const int r = rb + lane;
+                    int sl = 0;                           // first slice whose scan exceeds r
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        const int v = __shfl_sync(FULL, srow, sl + o - 1);
+                        if (v <= r) sl += o;
+                    }
+                    const int s_end = __shfl_sync(FULL, srow, sl);
+                    const int s_n = __shfl_sync(FULL, ns, sl);
+                    const int s_jl = __shfl_sync(FULL, jl, sl);
+                    const int dk = kc + sl;
+                    const int j = s_jl + r - (s_end - s_n), k = klo + dk;
+                    const int dj = j - jlo;
+                    int lo = 1, hi = 0;
+                    if (r < chunk_rows) row_interval(su->f, dj, dk, ilo, ihi, lo, hi);
+                    if (PASS == kPassImageBand) {
+                        // record the band part of each row (warp-aggregated append)
+                        int blo = 1, bhi = 0;
+                        if (hi >= lo) {
+                            const short2 br = __ldg(P.bandrow[side] + (k * ny + j));
+                            blo = max(lo, (int)br.x);
+                            bhi = min(hi, (int)br.y);
+                        }
+                        const bool band = blo <= bhi;
+                        const unsigned bm = __ballot_sync(FULL, band);
+                        if (bm) {
+                            const int pos = nband + __popc(bm & ((1u << lane) - 1u));
+                            if (band && pos < kBandRows) brec[pos] = pack_band_row(blo, bhi, j, k);
+                            nband += __popc(bm);
+                        }
+                    }
+                    const int cnt = max(0, hi - lo + 1);
+                    int incl = cnt;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int v = __shfl_up_sync(FULL, incl, o);
+                        if (lane >= o) incl += v;
+                    }
+                    const int batch_total = __shfl_sync(FULL, incl, 31);
+                    nvox += batch_total;
+                    // append the non-empty rows to the queue
+                    const unsigned ne = __ballot_sync(FULL, cnt > 0);
+                    if (cnt > 0) {
+                        // M = (a.x a.y a.z; a.w b.x b.y; b.z b.w c.x), s0 = c.yzw, t0 = t.xyz
+                        const float4 ma = ld_volatile_f4(sb + offsetof(RasterSetup, M));
+                        const float4 mb = ld_volatile_f4(sb + offsetof(RasterSetup, M) + 16);
+                        const float4 mc = ld_volatile_f4(sb + offsetof(RasterSetup, M) + 32);
+                        const float4 mt = ld_volatile_f4(sb + offsetof(RasterSetup, t0));
+                        const int q = (tail + __popc(ne & lt_mask)) & (kRowQ - 1);
+                        const int st = total + incl - cnt;
+                        const float dy = (float)j - mc.z, dz = (float)k - mc.w;
+                        Q.start[q] = st;
+                        Q.d[q] = lo - st;
+                        Q.base[q] = (k * ny + j) * nx;
+                        Q.rx[q] = fmaf(ma.y, dy, fmaf(ma.z, dz, mt.x));
+                        Q.ry[q] = fmaf(mb.x, dy, fmaf(mb.y, dz, mt.y));
+                        Q.rz[q] = fmaf(mb.w, dy, fmaf(mc.x, dz, mt.z));
+                    }
+                    tail += __popc(ne);
+                    total += batch_total;
+                    __syncwarp();
+                    while (total - pend >= kWin) {
+                        window(pend, kWin);
+                        pend += kWin;
+                        advance();
+                    }
                 }
             }
             if (total > pend) window(pend, total - pend);
