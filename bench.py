@@ -560,6 +560,7 @@ def run_surrogate_ea(args):
         "config": {"workload": f"c3: 256x256x160 f16, 1521 points / 6912 tets, population {P}, {G} generations x "
                                f"{R} mixing rounds, screen 4x (top 25% exactly evaluated)",
                    "network": f"{3 * V} -> 512 -> 256 -> 3, BF16 weights, FP32 accumulation, Adam",
+                   "screen_score": "sum over objectives of (net(candidate) - net(parent)) / std, lowest 25% kept",
                    "training_samples": n_samples, "epochs": args.epochs, "train_seconds": t_train},
         "hv_plain": plain["hv"], "hv_surrogate": sur["hv"], "hv_ratio": sur["hv"] / plain["hv"],
         "hv_plain_at_surrogate_budget": hv_plain_same_budget,

@@ -7,8 +7,10 @@ linkage subset (a breadth-first mesh neighbourhood of 4-32 points, the
 meshes; the partial solution is accepted if it dominates its parent or is
 non-dominated with respect to the elitist archive, and is not folded (Sec. 3;
 folded solutions are discarded, Sec. 4.3.1).  With a surrogate, all
-candidates of a round are first scored by the network and only the best
-``screen`` fraction is evaluated exactly; the rest are dropped unevaluated.
+candidates of a round are first scored by the network (the predicted change
+of each objective, as the difference of the network's outputs for the
+candidate and for its parent) and only the best ``screen`` fraction is
+evaluated exactly; the rest are dropped unevaluated.
 
 Hypervolume: exact 3-D, by sweeping the third objective over exact 2-D
 staircase areas.
@@ -122,6 +124,26 @@ def bfs_orders(tets: np.ndarray, n_points: int, depth: int = 32) -> np.ndarray:
     return out
 
 
+def acceptance_margin(pred: np.ndarray, parent: np.ndarray, archive: np.ndarray, scale: np.ndarray) -> np.ndarray:
+    """Predicted distance of each candidate from the acceptance test (lower is better).
+
+    A candidate is kept if it dominates its parent or no archived point
+    dominates it.  In units of ``scale`` per objective: max_k (y_k - p_k) is
+    negative when y is better than the parent p in every objective, and the
+    maximum over archived a of min_k (y_k - a_k) is negative exactly when no
+    archived point is at least as good as y in every objective (the archive
+    test).  The score is the smaller of the two, so the candidates that the
+    network places deepest inside the acceptance region come first.
+    """
+    y = pred / scale
+    m_parent = (y - parent / scale).max(axis=1)
+    if len(archive) == 0:
+        return np.full(len(y), -np.inf)
+    a = archive / scale
+    m_arch = (y[:, None, :] - a[None, :, :]).min(axis=2).max(axis=1)
+    return np.minimum(m_parent, m_arch)
+
+
 @dataclasses.dataclass
 class Surrogate:
     """Trained network + the standardisation of its targets."""
@@ -137,10 +159,18 @@ class Surrogate:
 def run(gp, prob, generations: int, rounds: int, seed: int, step_scale: np.ndarray,
         surrogate: Optional[Surrogate] = None, screen: float = 0.25, ref: Optional[np.ndarray] = None,
         hv_every: int = 10, log: Optional[List] = None, orders: Optional[np.ndarray] = None,
-        min_pts: int = 4, max_pts: int = 32) -> Dict:
+        min_pts: int = 4, max_pts: int = 32, random_screen: bool = False, differential: bool = True,
+        screen_rule: str = "sum") -> Dict:
     """Run the optimiser on the problem held by ``gp`` starting from ``prob``'s population.
 
-    step_scale: per-vertex standard deviation of a move (voxels).  log: if a
+    step_scale: per-vertex standard deviation of a move (voxels).
+    differential: predict a candidate's objectives as its parent's exact
+    objectives plus net(candidate) - net(parent) instead of net(candidate).
+    screen_rule: "sum" ranks by the predicted sum of standardised objective
+    changes (lowest first), "margin" by ``acceptance_margin``.
+    random_screen: without a surrogate, evaluate a random ``screen`` fraction
+    of the candidates (the same exact budget as the screened run, without the
+    network's choice).  log: if a
     list is given, (features, objectives) of every exact partial evaluation
     are appended (features as a device tensor).  Returns the archive, the
     hypervolume history, and the number of exact evaluations.
@@ -184,10 +214,23 @@ def run(gp, prob, generations: int, rounds: int, seed: int, step_scale: np.ndarr
                 dv = [torch.as_tensor(a).to(dev) for a in (slots_all, off, pts, new_s, new_t)]
                 feats = gp.partial_features(*dv)
             if surrogate is not None:
-                pred = surrogate.predict(feats)
-                score = ((pred - obj) / surrogate.std).sum(axis=1)
+                if differential:
+                    # the parent's own field through the same network: its
+                    # error is shared by parent and candidate and cancels
+                    dv = [torch.as_tensor(a).to(dev) for a in (slots_all, off, pts, cur_s[owner, pts],
+                                                               cur_t[owner, pts])]
+                    pred = obj + surrogate.predict(feats) - surrogate.predict(gp.partial_features(*dv))
+                else:
+                    pred = surrogate.predict(feats)
+                if screen_rule == "margin":
+                    score = acceptance_margin(pred, obj, archive.pts, surrogate.std)
+                else:
+                    score = ((pred - obj) / surrogate.std).sum(axis=1)
                 k = max(1, int(round(screen * P)))
                 chosen = np.sort(np.argsort(score, kind="stable")[:k]).astype(np.int32)
+            elif random_screen:
+                k = max(1, int(round(screen * P)))
+                chosen = np.sort(rng.choice(P, size=k, replace=False)).astype(np.int32)
             # exact partial evaluation of the chosen candidates
             sub_off = np.zeros(len(chosen) + 1, np.int32)
             sub_off[1:] = np.cumsum(np.diff(off)[chosen])

@@ -62,3 +62,26 @@ def test_bfs_orders_are_connected_neighbourhoods():
         assert o[0] == v and len(set(o)) == 12
         for k in range(1, 12):                                # each vertex touches an earlier one
             assert any(int(u) in adj[int(o[k])] for u in o[:k])
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_acceptance_margin_sign_matches_the_acceptance_rule(seed):
+    rng = np.random.default_rng(seed)
+    arch = ea.Archive()
+    for o in rng.integers(0, 8, size=(40, 3)).astype(float):
+        arch.add(o)
+    parents = rng.integers(0, 8, size=(300, 3)).astype(float)
+    cand = rng.integers(0, 8, size=(300, 3)).astype(float)
+    scale = np.array([1.0, 2.0, 0.5])
+    m = ea.acceptance_margin(cand, parents, arch.pts, scale)
+    for y, p, s in zip(cand, parents, m):
+        kept = arch.accepts(y) or ea.dominates(y, p)
+        strictly_better = bool(np.all(y < p))
+        # negative score: kept by the archive test or better in every objective
+        assert (s < 0) == (arch.accepts(y) or strictly_better)
+        if s < 0:
+            assert kept
+    # scaling an objective's unit does not change the sign
+    m2 = ea.acceptance_margin(cand * 3.0, parents * 3.0, arch.pts * 3.0, scale * 3.0)
+    np.testing.assert_allclose(m2, m, rtol=1e-12)
+    assert np.all(ea.acceptance_margin(cand, parents, np.zeros((0, 3)), scale) == -np.inf)
