@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--generations", type=int, default=200, help="c3: EA generations per run")
     ap.add_argument("--rounds", type=int, default=4, help="c3: mixing rounds per generation")
     ap.add_argument("--epochs", type=int, default=20, help="c3: surrogate training epochs")
+    ap.add_argument("--seeds", type=int, default=5, help="c3: EA seeds compared (200, 201, ...)")
     ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4"], default="c1",
                     help="c1: 128x128x96 f32 (the headline); c2: 256x256x160 f16 graded mesh; "
                          "c4: 16 uneven f16 problems in one batched graph launch")
@@ -75,6 +76,26 @@ def workload(seed_offset=0, name="c1"):
     rng = np.random.default_rng(4 + seed_offset)
     accept = [(rng.random(p.n_solutions) < 0.5).astype(np.uint8) for _ in range(ROUNDS)]
     return p, rounds, accept
+
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the timed
+# image pass (k_raster + k_guidance) per launch, averaged over one step's 21
+# launches, from an ncu capture of `bench.py --workload <w> --steps 1`.  Valid
+# only for the kernel source it was taken on (SHA-256 of k_raster.cu); after
+# any change to that file the bench reports null until it is re-measured.
+MEASURED_TRAFFIC = {
+    "c1": {"bytes_per_launch": 120295310, "k_raster_sha256": "bb90a82aaf02a912f0862728844052eda6f910e3b3fafbb37efe78f83b61d7c7"},
+}
+
+
+def measured_traffic(workload):
+    import hashlib
+    rec = MEASURED_TRAFFIC.get(workload)
+    if rec is None:
+        return None
+    with open(os.path.join(ROOT, "paper_2303_04873_gb300", "csrc", "k_raster.cu"), "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()
+    return rec["bytes_per_launch"] if sha == rec["k_raster_sha256"] else None
 
 
 def peaks():
@@ -204,21 +225,56 @@ def run_reference(args):
 # GPU
 # ---------------------------------------------------------------------------
 
+class Ranks:
+    """One process per GPU under torchrun: rank and world size from the
+    environment, a process group when world > 1, a barrier that also drains
+    the GPU, and the maximum of a time over ranks.  The replicas exchange
+    nothing else (the work shards by solution)."""
+
+    def __init__(self, backend: str = "nccl", gpu: bool = True):
+        self.gpu = gpu
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.backend = backend
+        self.dist = None
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend)
+            self.dist = dist
+
+    def barrier(self):
+        import torch
+        if self.dist is not None:
+            self.dist.barrier()
+        if self.gpu:
+            torch.cuda.synchronize()
+
+    def max(self, x: float) -> float:
+        if self.dist is None:
+            return float(x)
+        import torch
+        dev = torch.device("cuda", self.local) if self.backend == "nccl" else torch.device("cpu")
+        t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.destroy_process_group()
+
+
+def throughput(units_per_rank_step: float, steps: int, world: int, max_ms: float) -> float:
+    """Whole-job units/s: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank_step * steps / (max_ms / 1e3)
+
+
 def run_ours(args):
     import torch
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    ranks = Ranks("nccl")
+    rank, world, local = ranks.rank, ranks.world, ranks.local
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize()
+    barrier = ranks.barrier
 
     from paper_2303_04873_gb300 import build as _b
     _b.build()
@@ -305,13 +361,9 @@ def run_ours(args):
     raster_ms, raster_launches, _ = gp.profile_read()
     gp.profile(0)
     ck = clocks.stop()
-    total_ms = float(sum(step_ms))
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = ranks.max(float(sum(step_ms)))
     evals_per_step = n * (1 + ROUNDS)
-    value = world * evals_per_step * args.steps / (total_ms / 1e3)
+    value = throughput(evals_per_step, args.steps, world, total_ms)
     assert gp.device_status() == 0
 
     # ---- e2e through the C ABI with host buffers ----
@@ -358,12 +410,8 @@ def run_ours(args):
         b.synchronize()
         e2e_ms.append(a.elapsed_time(b))
     barrier()
-    e2e_total = float(sum(e2e_ms))
-    if dist is not None:
-        t = torch.tensor([e2e_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = world * evals_per_step * args.steps / (e2e_total / 1e3)
+    e2e_total = ranks.max(float(sum(e2e_ms)))
+    e2e_value = throughput(evals_per_step, args.steps, world, e2e_total)
 
     peak, peak_kind = peaks()
     achieved = visits_per_step * args.steps * bytes_per_visit / (raster_ms / 1e3) / 1e9
@@ -377,8 +425,9 @@ def run_ours(args):
                    "launch": {"blocks_per_sm": bps, "chunk": chunk},
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "kernel": "k_raster (rasterise + map + trilinear + h + guidance)",
+                     "frac": achieved / peak, "traffic": measured_traffic(args.workload),
+                     "traffic_unit": "bytes per launch (ncu, DRAM read + write)",
+                     "kernel": "image pass: k_raster (rasterise + map + trilinear + h) + k_guidance",
                      "peak_kind": f"{peak_kind} copy bandwidth",
                      "algorithmic_bytes": f"{bytes_per_visit} B per voxel visit x {visits_per_step} visits/step",
                      "kernel_ms_per_step": raster_ms / args.steps, "launches": raster_launches},
@@ -395,8 +444,7 @@ def run_ours(args):
     if rank == 0:
         print(json.dumps(line), flush=True)
     gp.close()
-    if dist is not None:
-        dist.destroy_process_group()
+    ranks.close()
     return 0
 
 
@@ -513,9 +561,11 @@ def local_step(p, frac=0.1):
 
 def run_surrogate_ea(args):
     """Surrogate pre-screen on the 1521-point FP16 problem: a plain run (seed
-    100) logs ~200k exact evaluations, the network is trained on them, then a
-    plain run and a surrogate-screened run (both seed 200, same reference
-    point) are compared on final hypervolume and exact evaluations."""
+    100) logs ~200k exact evaluations and the network is trained on them.
+    Then, for each of `--seeds` seeds (200, 201, ...), a plain run, a
+    surrogate-screened run and a randomly screened run (same exact budget as
+    the screened one) with the same hypervolume reference point are compared
+    on final hypervolume and exact evaluations."""
     import torch
     import synth
     from paper_2303_04873_gb300 import build as _b
@@ -544,30 +594,40 @@ def run_surrogate_ea(args):
     n_samples = int(feats.shape[0])
     del feats
     torch.cuda.empty_cache()
-    plain = ea.run(gp, p, G, R, seed=200, step_scale=step, orders=orders, hv_every=10)
-    sur = ea.run(gp, p, G, R, seed=200, step_scale=step, orders=orders, hv_every=10, surrogate=tr["surrogate"],
-                 ref=plain["ref"])
-    rnd = ea.run(gp, p, G, R, seed=200, step_scale=step, orders=orders, hv_every=10, random_screen=True,
-                 ref=plain["ref"])
-    # the plain run's hypervolume when it had used as many exact evaluations as the screened run
-    hx = np.array([h[1] for h in plain["history"]], float)
-    hv = np.array([h[2] for h in plain["history"]], float)
-    hv_plain_same_budget = float(np.interp(sur["exact"], hx, hv))
+    runs = []
+    for sd in range(200, 200 + args.seeds):
+        plain = ea.run(gp, p, G, R, seed=sd, step_scale=step, orders=orders, hv_every=10)
+        sur = ea.run(gp, p, G, R, seed=sd, step_scale=step, orders=orders, hv_every=10,
+                     surrogate=tr["surrogate"], ref=plain["ref"])
+        rnd = ea.run(gp, p, G, R, seed=sd, step_scale=step, orders=orders, hv_every=10, random_screen=True,
+                     ref=plain["ref"])
+        # the plain run's hypervolume when it had used as many exact evaluations as the screened run
+        hx = np.array([h[1] for h in plain["history"]], float)
+        hv = np.array([h[2] for h in plain["history"]], float)
+        runs.append({"seed": sd, "hv_plain": plain["hv"], "hv_surrogate": sur["hv"], "hv_random_screen": rnd["hv"],
+                     "hv_ratio": sur["hv"] / plain["hv"],
+                     "hv_plain_at_surrogate_budget": float(np.interp(sur["exact"], hx, hv)),
+                     "exact_plain": plain["exact"], "exact_surrogate": sur["exact"],
+                     "exact_random_screen": rnd["exact"],
+                     "history_plain": plain["history"], "history_surrogate": sur["history"]})
+    ratios = np.array([r["hv_ratio"] for r in runs])
+    exact_ratio = float(np.mean([r["exact_plain"] / r["exact_surrogate"] for r in runs]))
     line = {
         "metric": "surrogate-screened EA: exact-evaluation ratio at final hypervolume",
-        "value": plain["exact"] / sur["exact"], "unit": "x fewer exact evaluations",
+        "value": exact_ratio, "unit": "x fewer exact evaluations",
         "n_gpus": 1, "higher_is_better": True, "data": "synthetic", "dtype": "bf16 (network) / f32 (evaluator)",
         "config": {"workload": f"c3: 256x256x160 f16, 1521 points / 6912 tets, population {P}, {G} generations x "
-                               f"{R} mixing rounds, screen 4x (top 25% exactly evaluated)",
+                               f"{R} mixing rounds, screen 4x (top 25% exactly evaluated), "
+                               f"{args.seeds} seeds",
                    "network": f"{3 * V} -> 512 -> 256 -> 3, BF16 weights, FP32 accumulation, Adam",
                    "screen_score": "sum over objectives of (net(candidate) - net(parent)) / std, lowest 25% kept",
                    "training_samples": n_samples, "epochs": args.epochs, "train_seconds": t_train},
-        "hv_plain": plain["hv"], "hv_surrogate": sur["hv"], "hv_ratio": sur["hv"] / plain["hv"],
-        "hv_plain_at_surrogate_budget": hv_plain_same_budget,
-        "hv_random_screen": rnd["hv"], "exact_random_screen": rnd["exact"],
-        "exact_plain": plain["exact"], "exact_surrogate": sur["exact"],
+        "hv_ratio_mean": float(ratios.mean()), "hv_ratio_min": float(ratios.min()),
+        "hv_ratio_random_screen_mean": float(np.mean([r["hv_random_screen"] / r["hv_plain"] for r in runs])),
+        "hv_ratio_plain_at_surrogate_budget_mean": float(np.mean([r["hv_plain_at_surrogate_budget"] / r["hv_plain"]
+                                                                 for r in runs])),
         "surrogate_mae": tr["mae"].tolist(), "surrogate_r2": tr["r2"].tolist(),
-        "history_plain": plain["history"], "history_surrogate": sur["history"],
+        "runs": runs,
         "wall_seconds": time.perf_counter() - t0,
     }
     print(json.dumps(line), flush=True)

@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_raster(const DevProblem *__restri
     RowQueue &Q = rowq[threadIdx.x >> 5];
     const int n_ent = n_entries_dev ? min(*n_entries_dev, n_entries_host) : n_entries_host;
     const int n_items = 2 * n_ent;
-    run_items(n_items, chunk, queue, [&](const int item) {
+    run_items(n_items, chunk, queue + kQueueRaster, [&](const int item) {
         const int side = item >= n_ent ? 1 : 0;      // all source sides first, then all target sides
         const int e = item - side * n_ent;
         const RasterSetup *su = setup + 2 * (size_t)e + side;
@@ -571,12 +571,13 @@ __global__ void __launch_bounds__(kBlock, 4) k_raster(const DevProblem *__restri
             ro.n_vox = nvox;
             ro.n_gp = ngp;
             rout[2 * (size_t)e + side] = ro;
+            if (PASS == kPassImageBand && nband > 0) queue[kQueueList + atomicAdd(queue + kQueueListCount, 1)] = item;
         }
     });
 }
 
-// Continuous guidance (a6): for every (entry, side) with band rows, the band
-// voxels of those rows (rows recorded by the image pass, or recomputed when
+// Continuous guidance (a6): for every (entry, side) that the image pass listed
+// as having band rows, the band voxels of those rows (rows recorded by the image pass, or recomputed when
 // there were more than kBandRows; band voxels from the per-row sorted
 // list); writes e_guid and clears the count.  Mapped positions use the same
 // FP32 affine map as the image pass.
@@ -589,13 +590,14 @@ __global__ void __launch_bounds__(kBlock, 4) k_guidance(const DevProblem *__rest
 {
     const int lane = threadIdx.x & 31;
     const int n_ent = n_entries_dev ? min(*n_entries_dev, n_entries_host) : n_entries_host;
-    const int n_items = 2 * n_ent;
-    run_items(n_items, chunk, queue, [&](const int item) {
+    const int n_list = min(queue[kQueueListCount], 2 * n_ent);
+    const int *list = queue + kQueueList;
+    run_items(n_list, chunk, queue + kQueueGuidance, [&](const int li) {
+        const int item = list[li];
         const int side = item >= n_ent ? 1 : 0;
         const int e = item - side * n_ent;
         RasterOut *ro = rout + 2 * (size_t)e + side;
-        const int nband = ro->n_gp;                   // warp-uniform
-        if (nband == 0) return;
+        const int nband = ro->n_gp;                   // warp-uniform, > 0 for listed items
         const RasterSetup *su = setup + 2 * (size_t)e + side;
         const unsigned char *sb = reinterpret_cast<const unsigned char *>(su);
         const float4 m0 = __ldg(reinterpret_cast<const float4 *>(sb + offsetof(RasterSetup, M)));
@@ -711,7 +713,7 @@ cudaError_t launch_g(const DevProblem *probs, int g_mode, const WorkEntry *entri
                                                                     n_host, chunk, queue);
         if (cudaPeekAtLastError() == cudaSuccess)
             k_guidance<<<grid, kBlock, 0, st>>>(probs, entries, setup, rout, bandrows, n_dev, n_host, chunk,
-                                                queue + 1);
+                                                queue);
         break;
     case MOREA_G_PAIR_TRANSFER:
         k_raster<TI, HMODE, kPassImagePairs><<<grid, kBlock, 0, st>>>(probs, entries, setup, rout, bandrows, n_dev,
@@ -732,10 +734,8 @@ cudaError_t launch_raster(const DevProblem *probs, const DevProblem &hp, const W
                           int n_entries_host, int grid, int chunk, int *queue, cudaStream_t st)
 {
     if (grid <= 0) grid = sm_count() * 8;
-    if (chunk > 0) {
-        cudaError_t e = cudaMemsetAsync(queue, 0, 2 * sizeof(int), st);
-        if (e != cudaSuccess) return e;
-    }
+    cudaError_t e = cudaMemsetAsync(queue, 0, kQueueList * sizeof(int), st);
+    if (e != cudaSuccess) return e;
     if (hp.dtype == MOREA_F16) {
         if (hp.h_mode == MOREA_H_MOREA_FG)
             return launch_g<__half, MOREA_H_MOREA_FG>(probs, hp.g_mode, entries, setup, rout, bandrows, n_entries_dev,

@@ -319,7 +319,7 @@ morea_status morea_create_problem(const morea_problem_desc *d, void *stream, mor
     TRY(dalloc(p, &p->req_chg_q, 2 * (size_t)max_req * max_changed));
     TRY(dalloc(p, &p->dp, 1));
     TRY(dalloc(p, &p->visits, 1));
-    TRY(dalloc(p, &p->queue, 2));
+    TRY(dalloc(p, &p->queue, queue_ints(cap, continuous)));
 
     hp.img[0] = img[0];
     hp.img[1] = img[1];

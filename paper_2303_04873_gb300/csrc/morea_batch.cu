@@ -141,7 +141,7 @@ morea_status morea_batch_create(morea_problem *const *problems, int32_t n_proble
     if (e == cudaSuccess) e = dalloc(b, &b->tout, (size_t)cap);
     if (e == cudaSuccess && p0->hp.g_mode == MOREA_G_CONTINUOUS)
         e = dalloc(b, &b->bandrows, 2 * (size_t)cap * kBandRowsPerItem);
-    if (e == cudaSuccess) e = dalloc(b, &b->queue, 2);
+    if (e == cudaSuccess) e = dalloc(b, &b->queue, queue_ints(cap, p0->hp.g_mode == MOREA_G_CONTINUOUS));
     if (e == cudaSuccess)
         e = cudaMemcpy(b->dprobs, hps.data(), sizeof(DevProblem) * n_problems, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {

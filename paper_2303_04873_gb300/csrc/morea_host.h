@@ -29,7 +29,7 @@ struct morea_problem {
     int2 *bandrows = nullptr;
     morea::TetOut *tout = nullptr;
     int *counter = nullptr;
-    int *queue = nullptr;                 // 2 counters of the dynamic work queue
+    int *queue = nullptr;                 // work-queue counters + guidance item list (queue_ints)
     morea::ReqInfo *rinfo = nullptr;
     morea_totals *req_delta = nullptr;
     int *req_chg_pts = nullptr;

@@ -138,7 +138,17 @@ cudaError_t launch_build_quads(const DevProblem &hp, int side, void *quad, cudaS
 cudaError_t launch_band_rows(const DevProblem &hp, int side, short2 *bandrow, cudaStream_t st);
 // image pass (+ continuous guidance pass); bandrows: [2 * entries][kBandRowsPerItem] scratch
 constexpr int kBandRowsPerItem = 128;
-// chunk > 0 selects the atomic work queue (queue: 2 device counters, reset here)
+// chunk > 0 selects the atomic work queue.  queue: kQueueList device counters
+// (reset here) followed, in the continuous-guidance mode, by the list of the
+// (entry, side) items that have band rows (capacity 2 * n_entries_host).
+constexpr int kQueueRaster = 0;      // work counter of the image pass
+constexpr int kQueueGuidance = 1;    // work counter of the guidance pass
+constexpr int kQueueListCount = 2;   // items listed for the guidance pass
+constexpr int kQueueList = 4;        // first list entry (16-byte aligned)
+inline size_t queue_ints(long long cap_entries, bool continuous)
+{
+    return kQueueList + (continuous ? 2 * (size_t)cap_entries : 0);
+}
 cudaError_t launch_raster(const DevProblem *probs, const DevProblem &hp, const WorkEntry *entries,
                           const RasterSetup *setup, RasterOut *rout, int2 *bandrows, const int *n_entries_dev,
                           int n_entries_host, int grid, int chunk, int *queue, cudaStream_t st);
