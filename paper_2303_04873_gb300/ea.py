@@ -73,15 +73,37 @@ def hv3d(points: np.ndarray, ref) -> float:
     return vol
 
 
+def crowding(points: np.ndarray) -> np.ndarray:
+    """Crowding distance of each point: the sum over objectives of the gap
+    between its two neighbours in that objective, divided by the objective's
+    range; the extremes of every objective get infinity."""
+    n, m = points.shape
+    d = np.zeros(n)
+    for k in range(m):
+        order = np.argsort(points[:, k], kind="stable")
+        v = points[order, k]
+        span = v[-1] - v[0]
+        d[order[0]] = d[order[-1]] = np.inf
+        if n > 2 and span > 0:
+            d[order[1:-1]] += (v[2:] - v[:-2]) / span
+    return d
+
+
 class Archive:
-    """Elitist archive of non-dominated objective vectors (capacity-bounded)."""
+    """Elitist archive of non-dominated objective vectors.
+
+    Bounded by ``cap``: when it holds more than cap + cap // 4 points, the
+    points with the smallest crowding distance are dropped (recomputed after
+    each tenth of the excess) until cap remain, so the extremes and the
+    spread of the front are kept.
+    """
 
     def __init__(self, cap: int = 2000):
         self.cap = cap
         self.pts = np.zeros((0, 3))
 
     def accepts(self, o: np.ndarray) -> bool:
-        """True if no archived point dominates o (and o is not a duplicate)."""
+        """True if no archived point is at least as good as o in every objective."""
         if len(self.pts) == 0:
             return True
         le = np.all(self.pts <= o, axis=1)
@@ -92,9 +114,16 @@ class Archive:
             return False
         keep = ~(np.all(o <= self.pts, axis=1) & np.any(o < self.pts, axis=1))
         self.pts = np.vstack([self.pts[keep], o[None]])
-        if len(self.pts) > self.cap:
-            self.pts = self.pts[-self.cap:]
+        if len(self.pts) > self.cap + self.cap // 4:
+            self.prune()
         return True
+
+    def prune(self):
+        step = max(1, (len(self.pts) - self.cap) // 10)
+        while len(self.pts) > self.cap:
+            k = min(step, len(self.pts) - self.cap)
+            drop = np.argsort(crowding(self.pts), kind="stable")[:k]
+            self.pts = np.delete(self.pts, drop, axis=0)
 
 
 # ---------------------------------------------------------------------------

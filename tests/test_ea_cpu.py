@@ -85,3 +85,26 @@ def test_acceptance_margin_sign_matches_the_acceptance_rule(seed):
     m2 = ea.acceptance_margin(cand * 3.0, parents * 3.0, arch.pts * 3.0, scale * 3.0)
     np.testing.assert_allclose(m2, m, rtol=1e-12)
     assert np.all(ea.acceptance_margin(cand, parents, np.zeros((0, 3)), scale) == -np.inf)
+
+
+def test_crowding_distance_closed_form():
+    pts = np.array([[0.0, 4.0, 1.0], [1.0, 2.0, 1.0], [3.0, 1.0, 1.0], [4.0, 0.0, 1.0]])
+    d = ea.crowding(pts)
+    assert np.isinf(d[0]) and np.isinf(d[3])
+    # point 1: x neighbours 0 and 3 (range 4), y neighbours 1 and 4 (range 4), z constant
+    np.testing.assert_allclose(d[1:3], [3 / 4 + 3 / 4, 3 / 4 + 2 / 4])
+
+
+def test_archive_cap_keeps_extremes_and_non_dominance():
+    rng = np.random.default_rng(9)
+    arch = ea.Archive(cap=50)
+    t = rng.uniform(0, np.pi / 2, size=(400, 2))
+    front = np.stack([np.cos(t[:, 0]) * np.cos(t[:, 1]), np.sin(t[:, 0]) * np.cos(t[:, 1]), np.sin(t[:, 1])], 1)
+    for o in front:
+        arch.add(o)
+    assert len(arch.pts) <= 50 + 50 // 4
+    nd = ea.nondominated(arch.pts)
+    assert len(nd) == len(arch.pts)
+    # the per-objective minima of the whole front survive pruning
+    for k in range(3):
+        assert arch.pts[:, k].min() == pytest.approx(front[:, k].min())
