@@ -46,12 +46,6 @@ __device__ __forceinline__ float4 ld_volatile_f4(const unsigned char *p)
     return v;
 }
 
-__device__ __forceinline__ float2 ld_volatile_f2(const unsigned char *p)
-{
-    float2 v;
-    asm volatile("ld.global.nc.v2.f32 {%0,%1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
-    return v;
-}
 
 __device__ __forceinline__ float ld_img(const float *p, int idx) { return __ldg(p + idx); }
 __device__ __forceinline__ float ld_img(const __half *p, int idx) { return __half2float(__ldg(p + idx)); }
@@ -369,9 +363,9 @@ constexpr int kRowQ = 128;              // ring capacity (rows); power of two
 constexpr int kWin = 32;                // voxels per window (one per lane)
 struct RowQueue {
     int start[kRowQ];
-    int d[kRowQ];
-    int base[kRowQ];
-    float rx[kRowQ], ry[kRowQ], rz[kRowQ];
+    int2 db[kRowQ];                      // (d, base)
+    float4 r[kRowQ];                     // (rx, ry, rz, -)
+    float4 mcol;                         // first column of M and s0.x of the current item
 };
 
 // Image pass (a4, a5, a7): one warp per (entry, side).
@@ -387,6 +381,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_raster(const DevProblem *__restri
     __shared__ RowQueue rowq[kBlock / 32];
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
+    const unsigned upto = lane == 31 ? FULL : ((2u << lane) - 1u);   // bits 0..lane
     RowQueue &Q = rowq[threadIdx.x >> 5];
     const int n_ent = n_entries_dev ? min(*n_entries_dev, n_entries_host) : n_entries_host;
     const int n_items = 2 * n_ent;
@@ -411,6 +406,14 @@ __global__ void __launch_bounds__(kBlock, 4) k_raster(const DevProblem *__restri
             const int nyb = max(bx.w - jlo + 1, 1), nzb = bz2.y - klo + 1;
             const int n_rows = (ilo <= ihi && bx.w >= jlo && nzb > 0) ? nyb * nzb : 0;
             const bool inner = (valid & 2) != 0;
+            if (lane == 0) {
+                // first column of M (a.x, a.w, b.z) and s0.x (c.y)
+                const float4 ma = __ldg(reinterpret_cast<const float4 *>(sb + offsetof(RasterSetup, M)));
+                const float4 mb = __ldg(reinterpret_cast<const float4 *>(sb + offsetof(RasterSetup, M) + 16));
+                const float4 mc = __ldg(reinterpret_cast<const float4 *>(sb + offsetof(RasterSetup, M) + 32));
+                Q.mcol = make_float4(ma.x, ma.w, mb.z, mc.y);
+            }
+            __syncwarp();
             // row queue state (warp-uniform): live rows [head, tail), voxel
             // stream [pend, total) not yet processed
             int head = 0, tail = 0, pend = 0, total = 0;
@@ -438,14 +441,12 @@ __global__ void __launch_bounds__(kBlock, 4) k_raster(const DevProblem *__restri
                     if (st < wbase + 32) bit = 1u << (st - wbase);
                 }
                 const unsigned starts = __reduce_or_sync(FULL, bit);
-                const unsigned upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
                 const int q = (head + __popc(starts & upto)) & (kRowQ - 1);
                 if (lane < w) {
-                    // first column of M and s0.x: a.x, a.w, b.z, c.y
-                    const float4 ma = ld_volatile_f4(sb + offsetof(RasterSetup, M));
-                    const float2 mbz = ld_volatile_f2(sb + offsetof(RasterSetup, M) + 24);
-                    const float2 mcy = ld_volatile_f2(sb + offsetof(RasterSetup, M) + 32);
-                    voxel(wbase + lane, Q.d[q], Q.base[q], Q.rx[q], Q.ry[q], Q.rz[q], ma.x, ma.w, mbz.x, mcy.y);
+                    const int2 db = Q.db[q];
+                    const float4 r = Q.r[q];
+                    const float4 mc = Q.mcol;
+                    voxel(wbase + lane, db.x, db.y, r.x, r.y, r.z, mc.x, mc.y, mc.z, mc.w);
                 }
                 __syncwarp();
             };
@@ -536,11 +537,10 @@ __global__ void __launch_bounds__(kBlock, 4) k_raster(const DevProblem *__restri
                         const int st = total + incl - cnt;
                         const float dy = (float)j - mc.z, dz = (float)k - mc.w;
                         Q.start[q] = st;
-                        Q.d[q] = lo - st;
-                        Q.base[q] = (k * ny + j) * nx;
-                        Q.rx[q] = fmaf(ma.y, dy, fmaf(ma.z, dz, mt.x));
-                        Q.ry[q] = fmaf(mb.x, dy, fmaf(mb.y, dz, mt.y));
-                        Q.rz[q] = fmaf(mb.w, dy, fmaf(mc.x, dz, mt.z));
+                        Q.db[q] = make_int2(lo - st, (k * ny + j) * nx);
+                        Q.r[q] = make_float4(fmaf(ma.y, dy, fmaf(ma.z, dz, mt.x)),
+                                             fmaf(mb.x, dy, fmaf(mb.y, dz, mt.y)),
+                                             fmaf(mb.w, dy, fmaf(mc.x, dz, mt.z)), 0.0f);
                     }
                     tail += __popc(ne);
                     total += batch_total;
@@ -644,24 +644,18 @@ __global__ void __launch_bounds__(kBlock, 4) k_guidance(const DevProblem *__rest
                     dk += 1;
                 }
             }
-            // the band voxels of row (j, k) with lo <= x <= hi: positions [a, b) of the row's list
+            // the band voxels of row (j, k) with lo <= x <= hi: positions [a, a + cnt)
+            // of the row's list, from the per-voxel rank within the row
             int a = 0, cnt = 0;
             if (hi >= lo) {
                 const int row = k * ny + j;
-                int b0 = P.band_start[side][row], b1 = P.band_start[side][row + 1];
-                const short *bx_ = P.band_x[side];
-                int l = b0, r = b1;                   // first position with x >= lo
-                while (l < r) {
-                    const int m = (l + r) >> 1;
-                    if (bx_[m] < lo) l = m + 1; else r = m;
-                }
-                a = l;
-                r = b1;                               // first position with x > hi
-                while (l < r) {
-                    const int m = (l + r) >> 1;
-                    if (bx_[m] <= hi) l = m + 1; else r = m;
-                }
-                cnt = l - a;
+                const size_t rb = (size_t)row * nx;
+                const int b0 = __ldg(P.band_start[side] + row);
+                const int rlo = __ldg(P.band_rank[side] + rb + lo);
+                const int rhi = __ldg(P.band_rank[side] + rb + hi);
+                const int last = __ldg(P.band[side] + rb + hi) != 0 ? 1 : 0;
+                a = b0 + rlo;
+                cnt = rhi - rlo + last;
             }
             int incl = cnt;
 #pragma unroll

@@ -388,23 +388,32 @@ morea_status morea_create_problem(const morea_problem_desc *d, void *stream, mor
             TRY(cudaMemcpyAsync(hband.data(), band[s], (size_t)N, cudaMemcpyDeviceToHost, st));
             TRY(cudaStreamSynchronize(st));
             std::vector<int> start((size_t)ny * nz + 1, 0);
-            std::vector<short> xs;
+            std::vector<short> xs, rank((size_t)N);
             for (long long row = 0; row < (long long)ny * nz; ++row) {
                 const uint8_t *b = hband.data() + row * nx;
-                for (int x = 0; x < nx; ++x)
-                    if (b[x]) xs.push_back((short)x);
+                short before = 0;
+                for (int x = 0; x < nx; ++x) {
+                    rank[(size_t)row * nx + x] = before;
+                    if (b[x]) {
+                        xs.push_back((short)x);
+                        ++before;
+                    }
+                }
                 start[row + 1] = (int)xs.size();
             }
             int *bs = nullptr;
-            short *bxs = nullptr;
+            short *bxs = nullptr, *brk = nullptr;
             TRY(dalloc(p, &bs, start.size()));
             TRY(dalloc(p, &bxs, std::max<size_t>(xs.size(), 1)));
+            TRY(dalloc(p, &brk, (size_t)N));
             TRY(cudaMemcpyAsync(bs, start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice, st));
             if (!xs.empty())
                 TRY(cudaMemcpyAsync(bxs, xs.data(), sizeof(short) * xs.size(), cudaMemcpyHostToDevice, st));
+            TRY(cudaMemcpyAsync(brk, rank.data(), sizeof(short) * (size_t)N, cudaMemcpyHostToDevice, st));
             TRY(cudaStreamSynchronize(st));
             hp.band_start[s] = bs;
             hp.band_x[s] = bxs;
+            hp.band_rank[s] = brk;
         }
         TRY(cudaMemcpyAsync(p->dp, &hp, sizeof(DevProblem), cudaMemcpyHostToDevice, st));
     }

@@ -31,6 +31,7 @@ struct DevProblem {
     const short2 *bandrow[2];        // [nz*ny] x-range of band voxels in each image row (empty: x > y)
     const int *band_start[2];        // [nz*ny + 1] CSR of the band voxels of each image row
     const short *band_x[2];          // their x, ascending within a row
+    const short *band_rank[2];       // [N] band voxels before x in the same image row
     const int4 *tets;                // positively oriented topology
     const float *cdelta;             // elasticity factor per tet
     const int4 *gq[2];               // snapped guidance points per side
