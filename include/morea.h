@@ -293,6 +293,13 @@ morea_status morea_mlp_destroy(morea_mlp *n);
  * b1 [h1], W2 [h2][h1], b2 [h2], W3 [n_out][h2], b3 [n_out]. */
 morea_status morea_mlp_info(const morea_mlp *n, int64_t *n_params, int32_t *padded_inputs);
 
+/* Read and clear the network's device status word (synchronises the
+ * stream).  Bit 0 (MOREA_DEV_MLP_WAIT_TIMEOUT): a wait inside a
+ * tensor-core product gave up (its outputs are invalid).  No counterpart in
+ * the paper; the bounded waits are the kernels' own safeguard. */
+#define MOREA_DEV_MLP_WAIT_TIMEOUT 1u
+morea_status morea_mlp_device_status(morea_mlp *n, uint32_t *bits, void *stream);
+
 /* Copy the parameter vector in (resets the Adam state) / out.  host or device. */
 morea_status morea_mlp_set_params(morea_mlp *n, const float *params, void *stream);
 morea_status morea_mlp_get_params(morea_mlp *n, float *params, void *stream);

@@ -1,12 +1,11 @@
 // Surrogate network (step a10): a 3-layer perceptron n_in -> h1 -> h2 -> n_out
 // over the per-vertex displacements of a solution, with BF16 weights and
-// activations on the tensor cores and FP32 accumulation, trained on the GPU by
-// these kernels (forward, backward, Adam).
-//
-// Every dense product is written as C[M x N] = A[M x K] . B[N x K]^T with both
-// operands K-contiguous (the mma "row.col" form); transposes give the other
-// layouts.  K dimensions are padded with zeros to a multiple of 64 (features)
-// or 32 (batch), so the tiles never need a K bound check.
+// activations and FP32 accumulation, trained on the GPU by these kernels
+// (forward, backward, Adam).  The dense products C = A . B^T, both operands
+// K-contiguous, run on the tcgen05 tensor cores (k_gemm_tc.cu); this file
+// holds the element-wise and small kernels around them.  Transposes give the
+// K-contiguous layouts; K dimensions are padded with zeros to a multiple of
+// 64 (features) or 32 (batch).
 #include <cuda_bf16.h>
 
 #include "morea_internal.cuh"
@@ -18,134 +17,16 @@ namespace {
 
 using bf16 = __nv_bfloat16;
 
-constexpr int GBM = 128, GBN = 128, GBK = 32, GPAD = 8;
-constexpr int GSTR = GBK + GPAD;      // smem row stride in elements (80 bytes)
-
-__device__ __forceinline__ unsigned smem_u32(const void *p)
-{
-    return (unsigned)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool valid)
-{
-    const int bytes = valid ? 16 : 0;     // 0: zero-fill without reading
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(smem)), "l"(gmem), "r"(bytes));
-}
-
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
-
-__device__ __forceinline__ void ldsm_x4(unsigned &r0, unsigned &r1, unsigned &r2, unsigned &r3, const void *p)
-{
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(smem_u32(p)));
-}
-
-__device__ __forceinline__ void mma_bf16(float *c, const unsigned *a, unsigned b0, unsigned b1)
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// C = act(A . B^T + bias) (M x N), optionally masked by relu'(H) = [H > 0].
-// Tiles 128 x 128 x 32, 8 warps as 2 (M) x 4 (N), warp tile 64 x 32.
-__global__ void __launch_bounds__(256) k_gemm_nt(int M, int N, int K, const bf16 *__restrict__ A, int lda,
-                                                 const bf16 *__restrict__ B, int ldb, const float *__restrict__ bias,
-                                                 const bf16 *__restrict__ mask, int ldm, int relu, float *__restrict__ C,
-                                                 int ldc, bf16 *__restrict__ Cb, int ldcb)
-{
-    __shared__ __align__(16) bf16 As[2][GBM][GSTR];
-    __shared__ __align__(16) bf16 Bs[2][GBN][GSTR];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = (warp >> 2) * 64, wn = (warp & 3) * 32;
-    const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
-    float acc[4][4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.0f;
-
-    auto load_tile = [&](int buf, int k0) {
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            const int chunk = tid + c * 256;          // 512 chunks of 16 B per operand tile
-            const int r = chunk >> 2, kk = (chunk & 3) * 8;
-            const int ga = min(m0 + r, M - 1), gb = min(n0 + r, N - 1);
-            cp_async16(&As[buf][r][kk], A + (size_t)ga * lda + k0 + kk, m0 + r < M);
-            cp_async16(&Bs[buf][r][kk], B + (size_t)gb * ldb + k0 + kk, n0 + r < N);
-        }
-        cp_async_commit();
-    };
-
-    const int nk = K / GBK;
-    load_tile(0, 0);
-    for (int kt = 0; kt < nk; ++kt) {
-        const int buf = kt & 1;
-        if (kt + 1 < nk) {
-            load_tile(buf ^ 1, (kt + 1) * GBK);
-            cp_async_wait1();
-        } else {
-            cp_async_wait0();
-        }
-        __syncthreads();
-#pragma unroll
-        for (int ks = 0; ks < GBK; ks += 16) {
-            unsigned af[4][4], bfr[2][4];
-#pragma unroll
-            for (int mi = 0; mi < 4; ++mi)
-                ldsm_x4(af[mi][0], af[mi][1], af[mi][2], af[mi][3],
-                        &As[buf][wm + mi * 16 + (lane & 15)][ks + (lane >> 4) * 8]);
-#pragma unroll
-            for (int nj = 0; nj < 2; ++nj)
-                ldsm_x4(bfr[nj][0], bfr[nj][1], bfr[nj][2], bfr[nj][3],
-                        &Bs[buf][wn + nj * 16 + (lane >> 4) * 8 + (lane & 7)][ks + ((lane >> 3) & 1) * 8]);
-#pragma unroll
-            for (int mi = 0; mi < 4; ++mi)
-#pragma unroll
-                for (int ni = 0; ni < 4; ++ni)
-                    mma_bf16(acc[mi][ni], af[mi], bfr[ni >> 1][(ni & 1) * 2], bfr[ni >> 1][(ni & 1) * 2 + 1]);
-        }
-        __syncthreads();
-    }
-    const int g = lane >> 2, t = lane & 3;
-#pragma unroll
-    for (int mi = 0; mi < 4; ++mi)
-#pragma unroll
-        for (int ni = 0; ni < 4; ++ni)
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int m = m0 + wm + mi * 16 + g + h * 8;
-                if (m >= M) continue;
-#pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const int n = n0 + wn + ni * 8 + 2 * t + q;
-                    if (n >= N) continue;
-                    float v = acc[mi][ni][h * 2 + q];
-                    if (bias) v += bias[n];
-                    if (relu) v = fmaxf(v, 0.0f);
-                    if (mask && !(__bfloat162float(mask[(size_t)m * ldm + n]) > 0.0f)) v = 0.0f;
-                    if (C) C[(size_t)m * ldc + n] = v;
-                    if (Cb) Cb[(size_t)m * ldcb + n] = __float2bfloat16(v);
-                }
-            }
-}
-
 // FP32 [rows][cols] -> BF16 [rows][ld] with zero padding up to ld (and rows up to rows_pad).
-__global__ void k_to_bf16(int rows, int cols, int rows_pad, int ld, const float *__restrict__ x, bf16 *__restrict__ y)
+__global__ void k_to_bf16(int r0, int rows, int cols, int ld, const float *__restrict__ x, bf16 *__restrict__ y)
 {
-    const long long total = (long long)rows_pad * ld;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int r = (int)(i / ld), c = (int)(i - (long long)r * ld);
-        y[i] = __float2bfloat16(r < rows && c < cols ? x[(size_t)r * cols + c] : 0.0f);
-    }
+    const int r = r0 + blockIdx.y;                     // one row per grid row, columns in 2-element steps
+    const int c = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (c >= ld) return;
+    const float *xr = x + (size_t)r * cols;
+    const float a = r < rows && c < cols ? xr[c] : 0.0f;
+    const float b = r < rows && c + 1 < cols ? xr[c + 1] : 0.0f;
+    *reinterpret_cast<__nv_bfloat162 *>(y + (size_t)r * ld + c) = __floats2bfloat162_rn(a, b);
 }
 
 // out[c][r] = in[r][c] for r < rows (zero for rows <= r < rows_pad), c < cols.
@@ -201,21 +82,34 @@ __global__ void k_loss(int n, int n_out, const float *__restrict__ Y, const floa
     if (threadIdx.x == 0 && loss) atomicAdd(loss, sh[0] / (float)total);
 }
 
-// dW3[o][k] = sum_b dY[b][o] H2[b][k];  db3[o] = sum_b dY[b][o]
+// dW3[o][k] = sum_b dY[b][o] H2[b][k];  db3[o] = sum_b dY[b][o].
+// Block (32 columns k, 32 row groups) per (column tile, o); the 32 partial
+// sums are combined in a fixed order.
 __global__ void k_out_wgrad(int n, int h2, int n_out, const float *__restrict__ dY, const bf16 *__restrict__ H2, int ldh,
                             float *__restrict__ dW3, int ldw, float *__restrict__ db3)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n_out * h2) {
-        const int o = i / h2, k = i - o * h2;
-        float s = 0.0f;
-        for (int b = 0; b < n; ++b) s = fmaf(dY[(size_t)b * n_out + o], __bfloat162float(H2[(size_t)b * ldh + k]), s);
-        dW3[(size_t)o * ldw + k] = s;
-    } else if (i < n_out * h2 + n_out) {
-        const int o = i - n_out * h2;
-        float s = 0.0f;
-        for (int b = 0; b < n; ++b) s += dY[(size_t)b * n_out + o];
-        db3[o] = s;
+    __shared__ float part[32][33], pb[32];
+    const int o = blockIdx.y, k = blockIdx.x * 32 + threadIdx.x;
+    float s = 0.0f, sb = 0.0f;
+    for (int b = threadIdx.y; b < n; b += 32) {
+        const float d = dY[(size_t)b * n_out + o];
+        if (k < h2) s = fmaf(d, __bfloat162float(H2[(size_t)b * ldh + k]), s);
+        sb += d;
+    }
+    part[threadIdx.y][threadIdx.x] = s;
+    if (threadIdx.x == 0) pb[threadIdx.y] = sb;
+    __syncthreads();
+    if (threadIdx.y == 0) {
+        float t = 0.0f;
+#pragma unroll
+        for (int g = 0; g < 32; ++g) t += part[g][threadIdx.x];
+        if (k < h2) dW3[(size_t)o * ldw + k] = t;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            float u = 0.0f;
+#pragma unroll
+            for (int g = 0; g < 32; ++g) u += pb[g];
+            db3[o] = u;
+        }
     }
 }
 
@@ -234,14 +128,23 @@ __global__ void k_out_bgrad(int n, int h2, int n_out, const float *__restrict__ 
     }
 }
 
-// db[c] = sum_r D[r][c]  (column sums of a BF16 matrix, FP32)
+// db[c] = sum_r D[r][c]  (column sums of a BF16 matrix, FP32): 32 columns
+// per block, 32 row groups combined in a fixed order.
 __global__ void k_colsum(int rows, int cols, const bf16 *__restrict__ D, int ld, float *__restrict__ out)
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= cols) return;
+    __shared__ float part[32][33];
+    const int c = blockIdx.x * 32 + threadIdx.x;
     float s = 0.0f;
-    for (int r = 0; r < rows; ++r) s += __bfloat162float(D[(size_t)r * ld + c]);
-    out[c] = s;
+    if (c < cols)
+        for (int r = threadIdx.y; r < rows; r += 32) s += __bfloat162float(D[(size_t)r * ld + c]);
+    part[threadIdx.y][threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.y == 0 && c < cols) {
+        float t = 0.0f;
+#pragma unroll
+        for (int g = 0; g < 32; ++g) t += part[g][threadIdx.x];
+        out[c] = t;
+    }
 }
 
 // Adam on the FP32 master parameters, then the BF16 working copy.
@@ -271,18 +174,12 @@ inline int g1d(long long work) { return (int)std::max<long long>(1, std::min<lon
 
 }  // namespace
 
-cudaError_t mlp_gemm_nt(int M, int N, int K, const void *A, int lda, const void *B, int ldb, const float *bias,
-                        const void *mask, int ldm, int relu, float *C, int ldc, void *Cb, int ldcb, cudaStream_t st)
-{
-    dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM);
-    k_gemm_nt<<<grid, 256, 0, st>>>(M, N, K, (const bf16 *)A, lda, (const bf16 *)B, ldb, bias, (const bf16 *)mask, ldm,
-                                    relu, C, ldc, (bf16 *)Cb, ldcb);
-    return cudaGetLastError();
-}
-
 cudaError_t mlp_to_bf16(int rows, int cols, int rows_pad, int ld, const float *x, void *y, cudaStream_t st)
 {
-    k_to_bf16<<<g1d((long long)rows_pad * ld), 256, 0, st>>>(rows, cols, rows_pad, ld, x, (bf16 *)y);
+    if (ld % 2) return cudaErrorInvalidValue;
+    for (int r0 = 0; r0 < rows_pad; r0 += 65535)
+        k_to_bf16<<<dim3((ld / 2 + 255) / 256, std::min(65535, rows_pad - r0)), 256, 0, st>>>(r0, rows, cols, ld, x,
+                                                                                            (bf16 *)y);
     return cudaGetLastError();
 }
 
@@ -311,7 +208,8 @@ cudaError_t mlp_loss(int n, int n_out, const float *Y, const float *T, float *dY
 cudaError_t mlp_out_grads(int n, int h2, int n_out, const float *dY, const void *H2, int ldh, const void *W3, int ldw,
                           float *dW3, float *db3, void *dH2, int ldd, cudaStream_t st)
 {
-    k_out_wgrad<<<(n_out * h2 + n_out + 255) / 256, 256, 0, st>>>(n, h2, n_out, dY, (const bf16 *)H2, ldh, dW3, h2, db3);
+    k_out_wgrad<<<dim3((h2 + 31) / 32, n_out), dim3(32, 32), 0, st>>>(n, h2, n_out, dY, (const bf16 *)H2, ldh, dW3, h2,
+                                                                    db3);
     k_out_bgrad<<<g1d((long long)n * h2), 256, 0, st>>>(n, h2, n_out, dY, (const bf16 *)W3, ldw, (const bf16 *)H2, ldh,
                                                          (bf16 *)dH2, ldd);
     return cudaGetLastError();
@@ -319,7 +217,7 @@ cudaError_t mlp_out_grads(int n, int h2, int n_out, const float *dY, const void 
 
 cudaError_t mlp_colsum(int rows, int cols, const void *D, int ld, float *out, cudaStream_t st)
 {
-    k_colsum<<<(cols + 255) / 256, 256, 0, st>>>(rows, cols, (const bf16 *)D, ld, out);
+    k_colsum<<<(cols + 31) / 32, dim3(32, 32), 0, st>>>(rows, cols, (const bf16 *)D, ld, out);
     return cudaGetLastError();
 }
 

@@ -5,11 +5,16 @@
 
 namespace morea {
 
-// C = act(A . B^T + bias), A [M][K], B [N][K] BF16 (K a multiple of 32,
-// lda/ldb multiples of 8); optional ReLU, optional mask [H > 0] (BF16 H),
-// FP32 output C and/or BF16 output Cb.
+// C = act(A . B^T + bias) on the tcgen05 tensor cores (k_gemm_tc.cu):
+// A [M][K], B [N][K] BF16, 16-byte aligned, lda/ldb multiples of 8; optional
+// ReLU, optional mask [H > 0] (BF16 H), FP32 output C and/or BF16 output Cb.
+// A wait that gives up inside the kernel sets bit 0 of *status (device).
+// ws (ws_floats FP32, may be NULL) is the split-K workspace: products with
+// few output tiles and a long K are split over up to 8 CTAs per tile.
 cudaError_t mlp_gemm_nt(int M, int N, int K, const void *A, int lda, const void *B, int ldb, const float *bias,
-                        const void *mask, int ldm, int relu, float *C, int ldc, void *Cb, int ldcb, cudaStream_t st);
+                        const void *mask, int ldm, int relu, float *C, int ldc, void *Cb, int ldcb, float *ws,
+                        long long ws_floats, int *status, cudaStream_t st);
+int mlp_gemm_splits(int M, int N, int K);
 cudaError_t mlp_to_bf16(int rows, int cols, int rows_pad, int ld, const float *x, void *y, cudaStream_t st);
 cudaError_t mlp_transpose(int rows, int cols, int rows_pad, const void *in, int ldi, void *out, int ldo, cudaStream_t st);
 cudaError_t mlp_out_fwd(int n, int h2, int n_out, const void *H2, int ldh, const void *W3, int ldw, const float *b3,

@@ -22,6 +22,9 @@ struct morea_mlp {
     void *X = nullptr, *XT = nullptr, *H1 = nullptr, *H1T = nullptr, *H2 = nullptr;
     void *dH2 = nullptr, *dH2T = nullptr, *dH1 = nullptr, *dH1T = nullptr;
     float *Y = nullptr, *dY = nullptr, *loss = nullptr;
+    int *status = nullptr;                 // device status word (bit 0: a GEMM wait gave up)
+    float *ws = nullptr;                   // split-K workspace of the tensor-core products
+    long long ws_floats = 0;
     long long step = 0;
 };
 
@@ -46,10 +49,10 @@ cudaError_t forward(morea_mlp *n, int b, const float *x, cudaStream_t st)
     cudaError_t e = mlp_to_bf16(b, n->n_in, b, n->kin, x, n->X, st);
     if (e == cudaSuccess)
         e = mlp_gemm_nt(b, n->h1, n->kin, n->X, n->kin, n->W1b, n->kin, n->w + n->ob1, nullptr, 0, 1, nullptr, 0,
-                        n->H1, n->h1, st);
+                        n->H1, n->h1, n->ws, n->ws_floats, n->status, st);
     if (e == cudaSuccess)
         e = mlp_gemm_nt(b, n->h2, n->h1, n->H1, n->h1, n->W2b, n->h1, n->w + n->ob2, nullptr, 0, 1, nullptr, 0,
-                        n->H2, n->h2, st);
+                        n->H2, n->h2, n->ws, n->ws_floats, n->status, st);
     if (e == cudaSuccess) e = mlp_out_fwd(b, n->h2, n->n_out, n->H2, n->h2, n->W3b, n->h2, n->w + n->ob3, n->Y, st);
     return e;
 }
@@ -69,18 +72,18 @@ cudaError_t gradients(morea_mlp *n, int b, const float *x, const float *t, cudaS
     if (e == cudaSuccess) e = mlp_transpose(b, n->h1, n->bpad, n->H1, n->h1, n->H1T, n->bpad, st);
     if (e == cudaSuccess)
         e = mlp_gemm_nt(n->h2, n->h1, n->bpad, n->dH2T, n->bpad, n->H1T, n->bpad, nullptr, nullptr, 0, 0,
-                        n->g + n->oW2, n->h1, nullptr, 0, st);
+                        n->g + n->oW2, n->h1, nullptr, 0, n->ws, n->ws_floats, n->status, st);
     // dH1 = (dH2 W2) [H1 > 0]
     if (e == cudaSuccess)
         e = mlp_gemm_nt(b, n->h1, n->h2, n->dH2, n->h2, n->W2Tb, n->h2, nullptr, n->H1, n->h1, 0, nullptr, 0, n->dH1,
-                        n->h1, st);
+                        n->h1, n->ws, n->ws_floats, n->status, st);
     if (e == cudaSuccess) e = mlp_colsum(b, n->h1, n->dH1, n->h1, n->g + n->ob1, st);
     // dW1 = dH1^T X
     if (e == cudaSuccess) e = mlp_transpose(b, n->h1, n->bpad, n->dH1, n->h1, n->dH1T, n->bpad, st);
     if (e == cudaSuccess) e = mlp_transpose(b, n->kin, n->bpad, n->X, n->kin, n->XT, n->bpad, st);
     if (e == cudaSuccess)
         e = mlp_gemm_nt(n->h1, n->kin, n->bpad, n->dH1T, n->bpad, n->XT, n->bpad, nullptr, nullptr, 0, 0,
-                        n->g + n->oW1, n->kin, nullptr, 0, st);
+                        n->g + n->oW1, n->kin, nullptr, 0, n->ws, n->ws_floats, n->status, st);
     return e;
 }
 
@@ -154,6 +157,10 @@ morea_status morea_mlp_create(int32_t n_in, int32_t h1, int32_t h2, int32_t n_ou
     if (e == cudaSuccess) e = dalloc(n, &n->Y, B * n_out);
     if (e == cudaSuccess) e = dalloc(n, &n->dY, B * n_out);
     if (e == cudaSuccess) e = dalloc(n, &n->loss, 1);
+    if (e == cudaSuccess) e = dalloc(n, &n->status, 1);
+    n->ws_floats = 8LL * std::max(max_batch, h2) * h1;
+    if (e == cudaSuccess) e = dalloc(n, &n->ws, (size_t)n->ws_floats);
+    if (e == cudaSuccess) e = cudaMemset(n->status, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(n->w, 0, P * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(n->m, 0, P * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(n->v, 0, P * sizeof(float));
@@ -173,6 +180,20 @@ morea_status morea_mlp_info(const morea_mlp *n, int64_t *n_params, int32_t *padd
     if (n_params) *n_params = n->n_params;
     if (padded_inputs) *padded_inputs = n->kin;
     return MOREA_OK;
+}
+
+morea_status morea_mlp_device_status(morea_mlp *n, uint32_t *bits, void *stream)
+{
+    if (!n || !bits) return MOREA_EINVAL;
+    DeviceGuard g(n->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    int v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, n->status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(n->status, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    *bits = (uint32_t)v;
+    return from_cuda(e);
 }
 
 morea_status morea_mlp_set_params(morea_mlp *n, const float *params, void *stream)

@@ -37,7 +37,7 @@ ENTRY_POINTS = (
     "morea_commit_partial", "morea_check_folds", "morea_read_records", "morea_read_totals",
     "morea_partial_features", "morea_mlp_create", "morea_mlp_destroy", "morea_mlp_info",
     "morea_mlp_set_params", "morea_mlp_get_params", "morea_mlp_forward", "morea_mlp_gradients",
-    "morea_mlp_train_step",
+    "morea_mlp_train_step", "morea_mlp_device_status",
     "morea_device_status", "morea_problem_info", "morea_batch_create", "morea_batch_destroy",
     "morea_batch_eval_full", "morea_batch_capture", "morea_batch_replay", "morea_set_launch",
     "morea_batch_set_launch", "morea_profile", "morea_profile_read", "morea_fold_magnitude_noalloc",
@@ -108,6 +108,7 @@ def lib():
     L.morea_mlp_forward.argtypes = [vp, i32, vp, vp, vp]
     L.morea_mlp_gradients.argtypes = [vp, i32, vp, vp, vp, vp, vp]
     L.morea_mlp_train_step.argtypes = [vp, i32, vp, vp, ctypes.c_float, vp, vp]
+    L.morea_mlp_device_status.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32), vp]
     pa = ctypes.POINTER(ctypes.c_void_p)
     L.morea_batch_create.argtypes = [pa, i32, ctypes.POINTER(vp)]
     L.morea_batch_destroy.argtypes = [vp]
@@ -467,6 +468,12 @@ class Mlp:
             self.close()
         except Exception:
             pass
+
+    def device_status(self) -> int:
+        """Read and clear the network's device status bits (0: all waits completed)."""
+        bits = ctypes.c_uint32()
+        _check(lib().morea_mlp_device_status(self._h, ctypes.byref(bits), _stream(None)), "morea_mlp_device_status")
+        return bits.value
 
     def set_params(self, params):
         if isinstance(params, torch.Tensor):

@@ -1,5 +1,6 @@
-"""Surrogate network kernels (tensor-core GEMMs, backward, Adam) against the
-FP64 oracle of oracle/mlp.py with the same bfloat16-rounded operands.
+"""Surrogate network kernels (tcgen05 tensor-core products, backward, Adam)
+against the FP64 oracle of oracle/mlp.py with the same bfloat16-rounded
+operands.
 
 Tolerances (BF16 storage, FP32 accumulation): forward outputs within 5e-3 of
 the oracle in relative norm, each gradient block within 2e-2, one Adam step
@@ -51,6 +52,8 @@ def test_forward_and_gradients_match_oracle(mo, n_in, h1, h2, n_out, batch):
     # padded input columns get no gradient
     W1g = g[:h1 * net.kin].reshape(h1, net.kin)
     assert np.all(W1g[:, n_in:] == 0.0)
+    # every wait inside the tensor-core products completed
+    assert net.device_status() == 0
 
 
 def test_adam_step_matches_oracle(mo):
@@ -83,6 +86,7 @@ def test_training_fits_a_teacher(mo):
     pred = net.forward(x)
     final = float(((pred - y) ** 2).mean().item())
     assert final < first / 10, (first, final)
+    assert net.device_status() == 0 and teacher.device_status() == 0
 
 
 def test_partial_features(mo):
