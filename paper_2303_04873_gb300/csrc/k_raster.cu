@@ -37,16 +37,6 @@ struct QuadOf<__half> {
     using T = uint2;
 };
 
-// Loads of per-item constants where they are used (volatile, so they are not
-// hoisted into registers that would stay live across the whole item).
-__device__ __forceinline__ float4 ld_volatile_f4(const unsigned char *p)
-{
-    float4 v;
-    asm volatile("ld.global.nc.v4.f32 {%0,%1,%2,%3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
-    return v;
-}
-
-
 __device__ __forceinline__ float ld_img(const float *p, int idx) { return __ldg(p + idx); }
 __device__ __forceinline__ float ld_img(const __half *p, int idx) { return __half2float(__ldg(p + idx)); }
 
@@ -198,27 +188,31 @@ __device__ __forceinline__ void row_interval(const FaceRow *__restrict__ f, int 
     const float fdj = (float)dj, fdk = (float)dk;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        const float4 es = __ldg(reinterpret_cast<const float4 *>(&f[q].e0));       // e0, ey, ez, tol
-        const longlong2 ab = __ldg(reinterpret_cast<const longlong2 *>(&f[q].ax));  // ax, b00
+        const float4 es = __ldg(reinterpret_cast<const float4 *>(&f[q].e0));       // e0, ey, ez, signed tol
+        if (isinf(es.w)) {                    // face parallel to x: the whole row or nothing
+            const longlong2 ab = __ldg(reinterpret_cast<const longlong2 *>(&f[q].ax));
+            const longlong2 yz = __ldg(reinterpret_cast<const longlong2 *>(&f[q].by));
+            if (ab.y + yz.x * dj + yz.y * dk <= 0) hi = lo - 1;
+            continue;
+        }
         const float est = fmaf(es.y, fdj, fmaf(es.z, fdk, es.x));
-        const float tol = es.w;
+        const float tol = fabsf(es.w);
         const float fl = floorf(est);
         const float fr = est - fl;
-        if (ab.x > 0) {                       // inside for i > root: lo = floor(root) + 1
+        if (es.w > 0.0f) {                    // ax > 0, inside for i > root: lo = floor(root) + 1
             if (est + tol < (float)ilo) continue;
             if (est - tol >= (float)ihi) { hi = lo - 1; continue; }
             if (fr > tol && fr < 1.0f - tol) { lo = max(lo, (int)fl + 1); continue; }
+            const longlong2 ab = __ldg(reinterpret_cast<const longlong2 *>(&f[q].ax));
             const longlong2 yz = __ldg(reinterpret_cast<const longlong2 *>(&f[q].by));
             lo = max(lo, face_lo(ab.x, ab.y + yz.x * dj + yz.y * dk, est, ilo, ihi));
-        } else if (ab.x < 0) {                // inside for i < root: hi = ceil(root) - 1
+        } else {                              // ax < 0, inside for i < root: hi = ceil(root) - 1
             if (est - tol > (float)ihi) continue;
             if (est + tol <= (float)ilo) { hi = lo - 1; continue; }
             if (fr > tol && fr < 1.0f - tol) { hi = min(hi, (int)fl); continue; }
+            const longlong2 ab = __ldg(reinterpret_cast<const longlong2 *>(&f[q].ax));
             const longlong2 yz = __ldg(reinterpret_cast<const longlong2 *>(&f[q].by));
             hi = min(hi, face_hi(ab.x, ab.y + yz.x * dj + yz.y * dk, est, ilo, ihi));
-        } else {                              // face parallel to x: the whole row or nothing
-            const longlong2 yz = __ldg(reinterpret_cast<const longlong2 *>(&f[q].by));
-            if (ab.y + yz.x * dj + yz.y * dk <= 0) hi = lo - 1;
         }
     }
 }
@@ -366,6 +360,7 @@ struct RowQueue {
     int2 db[kRowQ];                      // (d, base)
     float4 r[kRowQ];                     // (rx, ry, rz, -)
     float4 mcol;                         // first column of M and s0.x of the current item
+    float4 rowc[3];                      // per map row a: (M[a][1], M[a][2], t0[a], s0.y | s0.z | -)
 };
 
 // Image pass (a4, a5, a7): one warp per (entry, side).
@@ -407,11 +402,15 @@ __global__ void __launch_bounds__(kBlock, 4) k_raster(const DevProblem *__restri
             const int n_rows = (ilo <= ihi && bx.w >= jlo && nzb > 0) ? nyb * nzb : 0;
             const bool inner = (valid & 2) != 0;
             if (lane == 0) {
-                // first column of M (a.x, a.w, b.z) and s0.x (c.y)
+                // M = (a.x a.y a.z; a.w b.x b.y; b.z b.w c.x), s0 = c.yzw, t0 = t.xyz
                 const float4 ma = __ldg(reinterpret_cast<const float4 *>(sb + offsetof(RasterSetup, M)));
                 const float4 mb = __ldg(reinterpret_cast<const float4 *>(sb + offsetof(RasterSetup, M) + 16));
                 const float4 mc = __ldg(reinterpret_cast<const float4 *>(sb + offsetof(RasterSetup, M) + 32));
+                const float4 mt = __ldg(reinterpret_cast<const float4 *>(sb + offsetof(RasterSetup, t0)));
                 Q.mcol = make_float4(ma.x, ma.w, mb.z, mc.y);
+                Q.rowc[0] = make_float4(ma.y, ma.z, mt.x, mc.z);
+                Q.rowc[1] = make_float4(mb.x, mb.y, mt.y, mc.w);
+                Q.rowc[2] = make_float4(mb.w, mc.x, mt.z, 0.0f);
             }
             __syncwarp();
             // row queue state (warp-uniform): live rows [head, tail), voxel
@@ -528,19 +527,15 @@ __global__ void __launch_bounds__(kBlock, 4) k_raster(const DevProblem *__restri
                     // append the non-empty rows to the queue
                     const unsigned ne = __ballot_sync(FULL, cnt > 0);
                     if (cnt > 0) {
-                        // M = (a.x a.y a.z; a.w b.x b.y; b.z b.w c.x), s0 = c.yzw, t0 = t.xyz
-                        const float4 ma = ld_volatile_f4(sb + offsetof(RasterSetup, M));
-                        const float4 mb = ld_volatile_f4(sb + offsetof(RasterSetup, M) + 16);
-                        const float4 mc = ld_volatile_f4(sb + offsetof(RasterSetup, M) + 32);
-                        const float4 mt = ld_volatile_f4(sb + offsetof(RasterSetup, t0));
+                        // the row's part of the map: r_a = M[a][1] dy + M[a][2] dz + t0[a]
+                        const float4 c0 = Q.rowc[0], c1 = Q.rowc[1], c2 = Q.rowc[2];
                         const int q = (tail + __popc(ne & lt_mask)) & (kRowQ - 1);
                         const int st = total + incl - cnt;
-                        const float dy = (float)j - mc.z, dz = (float)k - mc.w;
+                        const float dy = (float)j - c0.w, dz = (float)k - c1.w;
                         Q.start[q] = st;
                         Q.db[q] = make_int2(lo - st, (k * ny + j) * nx);
-                        Q.r[q] = make_float4(fmaf(ma.y, dy, fmaf(ma.z, dz, mt.x)),
-                                             fmaf(mb.x, dy, fmaf(mb.y, dz, mt.y)),
-                                             fmaf(mb.w, dy, fmaf(mc.x, dz, mt.z)), 0.0f);
+                        Q.r[q] = make_float4(fmaf(c0.x, dy, fmaf(c0.y, dz, c0.z)), fmaf(c1.x, dy, fmaf(c1.y, dz, c1.z)),
+                                             fmaf(c2.x, dy, fmaf(c2.y, dz, c2.z)), 0.0f);
                     }
                     tail += __popc(ne);
                     total += batch_total;

@@ -155,11 +155,14 @@ __device__ __forceinline__ void make_setup(const int4 *own, const int4 *oth, con
             fr.ez = (float)((double)fr.bz * inv);
             // |estimate - root| <= 2^-24 (3 |e0| + 3 |ey| dj + 3 |ez| dk) (rounding
             // of e0, ey, ez and of the two FMAs); 2^-20 leaves a factor 5 margin
-            fr.tol = (fabsf(fr.e0) + fabsf(fr.ey) * (float)nyb1 + fabsf(fr.ez) * (float)nzb1 + 1.0f) *
-                     (1.0f / 1048576.0f);
+            // stored with the sign of ax, so the row test needs no int64 load
+            // to know on which side of the root the inside lies
+            const float tol = (fabsf(fr.e0) + fabsf(fr.ey) * (float)nyb1 + fabsf(fr.ez) * (float)nzb1 + 1.0f) *
+                              (1.0f / 1048576.0f);
+            fr.tol = nx > 0 ? tol : -tol;
         } else {
             fr.e0 = fr.ey = fr.ez = 0.0f;
-            fr.tol = 0.0f;
+            fr.tol = INFINITY;                // face parallel to x: exact test of the whole row
         }
         su.f[f] = fr;
     }

@@ -55,7 +55,8 @@ struct __align__(16) WorkEntry {
 // centre (i, j, k) is inside w.r.t. f iff  ax i + b00 + by dj + bz dk > 0
 // (dj = j - jlo, dk = k - klo; integers, simulation-of-simplicity tie bit
 // folded into b00).  e0 + ey dj + ez dk estimates the root -B/A in FP32 to
-// within tol for every row of the bounding box (a rigorous bound).
+// within |tol| for every row of the bounding box (a rigorous bound); tol
+// carries the sign of ax, and is +infinity when ax = 0.
 struct __align__(16) FaceRow {
     long long ax, b00, by, bz;
     float e0, ey, ez, tol;
