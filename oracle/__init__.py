@@ -43,7 +43,8 @@ class _Problem(ctypes.Structure):
         ("guid_s", ctypes.c_void_p), ("guid_t", ctypes.c_void_p), ("guid_group", ctypes.c_void_p),
         ("trunc_radius", ctypes.c_double),
         ("h_mode", ctypes.c_int32), ("g_mode", ctypes.c_int32),
-        ("subvoxel_bits", ctypes.c_int32), ("pad1", ctypes.c_int32),
+        ("subvoxel_bits", ctypes.c_int32), ("estimator", ctypes.c_int32),
+        ("sampling_rate", ctypes.c_double),
     ]
 
 
@@ -110,6 +111,14 @@ def lib():
         L.orc_trilinear.restype = ctypes.c_double
         L.orc_h.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double]
         L.orc_h.restype = ctypes.c_double
+        L.orc_sobol.argtypes = [ctypes.c_uint64, ctypes.c_int]
+        L.orc_sobol.restype = ctypes.c_uint32
+        L.orc_fnv1a64.argtypes = [ctypes.c_void_p, ctypes.c_size_t]
+        L.orc_fnv1a64.restype = ctypes.c_uint64
+        L.orc_splitmix64.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
+        L.orc_splitmix64.restype = ctypes.c_uint64
+        L.orc_copy_shifts.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        L.orc_sample_lambda.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]
         _lib = L
     return _lib
 
@@ -120,6 +129,13 @@ def _ptr(a: Optional[np.ndarray]):
 
 class OracleError(RuntimeError):
     pass
+
+
+def getattr_default(g, name, default):
+    try:
+        return g(name)
+    except AttributeError:
+        return default
 
 
 class Oracle:
@@ -159,7 +175,9 @@ class Oracle:
                      tissue_factor=_ptr(tis), n_labels=0 if tis is None else int(tis.shape[0]),
                      n_guid=n_guid, guid_s=_ptr(gs), guid_t=_ptr(gt), guid_group=_ptr(gg),
                      trunc_radius=float(g("trunc_radius")), h_mode=int(g("h_mode")),
-                     g_mode=int(g("g_mode")), subvoxel_bits=int(g("subvoxel_bits")), pad1=0)
+                     g_mode=int(g("g_mode")), subvoxel_bits=int(g("subvoxel_bits")),
+                     estimator=int(getattr_default(g, "estimator", 0)),
+                     sampling_rate=float(np.float32(getattr_default(g, "sampling_rate", 1.0))))
         self._P = P
         self.nx, self.ny, self.nz = nx, ny, nz
         self.n_points = int(ref.shape[0])
@@ -262,3 +280,34 @@ def trilinear(img: np.ndarray, y) -> float:
 
 def h(mode: int, a: float, b: float) -> float:
     return float(lib().orc_h(mode, a, b))
+
+
+# -- the sampled estimator (R13) ---------------------------------------------
+
+def sobol(j: int, d: int) -> int:
+    """Coordinate d (0..3) of the unshifted Sobol point with Gray-code index j, as uint32."""
+    return int(lib().orc_sobol(j, d))
+
+
+def fnv1a64(data: bytes) -> int:
+    buf = ctypes.create_string_buffer(data, len(data))
+    return int(lib().orc_fnv1a64(ctypes.cast(buf, ctypes.c_void_p), len(data)))
+
+
+def splitmix64_outputs(state: int, n: int):
+    s = ctypes.c_uint64(state)
+    return [int(lib().orc_splitmix64(ctypes.byref(s))) for _ in range(n)]
+
+
+def copy_shifts(tet12) -> np.ndarray:
+    t = np.ascontiguousarray(tet12, dtype=np.int64).reshape(12)
+    out = np.zeros(4, np.uint32)
+    lib().orc_copy_shifts(_ptr(t), _ptr(out))
+    return out
+
+
+def sample_lambda(shift, j: int) -> np.ndarray:
+    sh = np.ascontiguousarray(shift, dtype=np.uint32).reshape(4)
+    out = np.zeros(4, np.float64)
+    lib().orc_sample_lambda(_ptr(sh), int(j), _ptr(out))
+    return out

@@ -55,6 +55,21 @@
  *      (affine map t0 + M (p - s0) with M = F adj(E) / D rounded to float,
  *      clamped cell, fused multiply-add lerps) and only its comparison with
  *      0 is used; the value (a - b)^2 itself is the FP64 sample.
+ *   R13 sampled estimator (App. A.2, the paper's own estimator; estimator =
+ *      1).  Per tet copy with orient D > 0: N = floor(rate * vol + 1/2)
+ *      points (capped at 2^24), vol = D / (6 2^3k) voxel^3 in FP64, rate the
+ *      given float.  Point j = 0 .. N-1 takes the 4-D Sobol point of
+ *      Gray-code index j (Joe-Kuo direction numbers; natural index
+ *      j ^ (j >> 1)), each 32-bit coordinate XOR-ed with a digital shift
+ *      derived from the copy's coordinates: FNV-1a (64-bit) over the copy's
+ *      12 snapped coordinates as little-endian int32 words, vertex by vertex,
+ *      then shift_d = high 32 bits of the (d+1)-th splitmix64 output from
+ *      that state.  u_d = (x_d + 1/2) 2^-32, e_d = -log u_d, lambda_d =
+ *      e_d / sum e (uniform on the tet), p = sum lambda_d v_d on the own
+ *      copy and T(p) = sum lambda_d w_d on the other (voxel units); both
+ *      images are sampled trilinearly (R4), and h, the guidance term (own
+ *      map sampled at p) and the counts (N per copy) enter as in the voxel
+ *      estimator.  Only h_mode PLAIN_SSD.
  */
 #include <math.h>
 #include <stdint.h>
@@ -66,6 +81,7 @@
 #define ORC_ENOMEM 2
 
 #define ORC_MAX_GROUPS 8
+#define ORC_MAX_SAMPLES (1LL << 24)
 
 typedef struct { int64_t x, y, z; } orc_i3;
 
@@ -84,7 +100,8 @@ typedef struct {
     const float *guid_t;
     const int32_t *guid_group;      /* [n_guid] or NULL */
     double trunc_radius;            /* <= 0: 2.5% of nx */
-    int32_t h_mode, g_mode, subvoxel_bits, pad1;
+    int32_t h_mode, g_mode, subvoxel_bits, estimator;   /* estimator: 0 voxels (R3), 1 samples (R13) */
+    double sampling_rate;           /* R13: points per voxel^3 (the float value given) */
 } orc_problem;
 
 typedef struct {
@@ -303,12 +320,16 @@ static void bary_map(const orc_state *st, const orc_i3 own[4], int64_t D, const 
 /* One side of one tet: side 0 samples source voxels in the source copy and
  * compares with the target image at T(p); side 1 is the symmetric term with
  * T' (the two sums of f_intensity and the two g terms of f_guidance). */
+static void eval_side_sampled(const orc_state *st, const orc_i3 own[4], const orc_i3 oth[4], int side,
+                              orc_tet *rec);
+
 static void eval_side(const orc_state *st, const orc_i3 own[4], const orc_i3 oth[4], int side,
                       orc_tet *rec)
 {
     const orc_problem *P = &st->p;
     int64_t D = orient_arr(own);
     if (D <= 0) return;                                /* R3: folded copy not rasterised */
+    int sampled = P->estimator == 1;
     const double *img_own = side == 0 ? P->img_s : P->img_t;
     const double *img_oth = side == 0 ? P->img_t : P->img_s;
     int64_t S = st->S, H = st->S / 2;
@@ -328,6 +349,7 @@ static void eval_side(const orc_state *st, const orc_i3 own[4], const orc_i3 oth
     }
     double e_img = 0.0, e_guid = 0.0;
     int64_t nv = 0;
+    if (!sampled)                                     /* R3 voxel sums; R13 sums below */
     for (int64_t k = lo[2]; k <= hi[2]; ++k)
         for (int64_t j = lo[1]; j <= hi[1]; ++j)
             for (int64_t i = lo[0]; i <= hi[0]; ++i) {
@@ -370,6 +392,151 @@ static void eval_side(const orc_state *st, const orc_i3 own[4], const orc_i3 oth
     rec->e_guid[side] = e_guid;
     rec->n_vox[side] = nv;
     rec->n_gp[side] = ngp;
+    if (sampled) eval_side_sampled(st, own, oth, side, rec);   /* R13 replaces the voxel sums */
+}
+
+/* ------------------------------------------------------------------ */
+/* R13: the sampled estimator of App. A.2                              */
+/* ------------------------------------------------------------------ */
+
+/* Sobol direction numbers V[d][b] (32-bit) of the first four dimensions:
+ * d = 0 is the van der Corput sequence; d = 1, 2, 3 use the primitive
+ * polynomials x + 1, x^2 + x + 1, x^3 + x + 1 (degree s, inner coefficients
+ * a) with initial numbers m = {1}, {1, 3}, {1, 3, 1} (Joe and Kuo's table),
+ * continued by m_k = m_{k-s} ^ (m_{k-s} << s) ^ sum_i a_i (m_{k-i} << i). */
+static uint32_t sobol_v[4][32];
+static int sobol_ready = 0;
+
+static void sobol_init(void)
+{
+    if (sobol_ready) return;
+    static const int deg[4] = {0, 1, 2, 3};
+    static const int poly[4] = {0, 0, 1, 1};
+    static const uint32_t m0[4][3] = {{0, 0, 0}, {1, 0, 0}, {1, 3, 0}, {1, 3, 1}};
+    for (int b = 0; b < 32; ++b) sobol_v[0][b] = 1u << (31 - b);
+    for (int d = 1; d < 4; ++d) {
+        int s = deg[d];
+        uint32_t m[33];
+        for (int k = 1; k <= s; ++k) m[k] = m0[d][k - 1];
+        for (int k = s + 1; k <= 32; ++k) {
+            uint32_t v = m[k - s] ^ (m[k - s] << s);
+            for (int i = 1; i < s; ++i)
+                if ((poly[d] >> (s - 1 - i)) & 1) v ^= m[k - i] << i;
+            m[k] = v;
+        }
+        for (int k = 1; k <= 32; ++k) sobol_v[d][k - 1] = m[k] << (32 - k);
+    }
+    sobol_ready = 1;
+}
+
+/* Coordinate d of the Sobol point with Gray-code index j (unshifted). */
+static uint32_t sobol_gray(uint64_t j, int d)
+{
+    uint64_t n = j ^ (j >> 1);
+    uint32_t x = 0;
+    for (int b = 0; n != 0 && b < 32; ++b, n >>= 1)
+        if (n & 1) x ^= sobol_v[d][b];
+    return x;
+}
+
+static uint64_t fnv1a64(const uint8_t *p, size_t n)
+{
+    uint64_t h = 0xcbf29ce484222325ULL;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 0x100000001b3ULL;
+    }
+    return h;
+}
+
+/* splitmix64: advance the state by the golden-ratio increment, then mix. */
+static uint64_t splitmix64_next(uint64_t *state)
+{
+    uint64_t z = (*state += 0x9E3779B97F4A7C15ULL);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* Digital shifts of one tet copy, from its snapped coordinates. */
+static void copy_shifts(const orc_i3 v[4], uint32_t shift[4])
+{
+    uint8_t bytes[48];
+    for (int i = 0; i < 4; ++i) {
+        int64_t c[3] = {v[i].x, v[i].y, v[i].z};
+        for (int a = 0; a < 3; ++a) {
+            uint32_t w = (uint32_t)(int32_t)c[a];
+            for (int q = 0; q < 4; ++q) bytes[12 * i + 4 * a + q] = (uint8_t)(w >> (8 * q));
+        }
+    }
+    uint64_t state = fnv1a64(bytes, sizeof(bytes));
+    for (int d = 0; d < 4; ++d) shift[d] = (uint32_t)(splitmix64_next(&state) >> 32);
+}
+
+/* Barycentric coordinates of sample j of a copy with the given shifts. */
+static void sample_lambda(const uint32_t shift[4], uint64_t j, double lam[4])
+{
+    double e[4], sum = 0.0;
+    for (int d = 0; d < 4; ++d) {
+        uint32_t x = sobol_gray(j, d) ^ shift[d];
+        double u = ((double)x + 0.5) / 4294967296.0;
+        e[d] = -log(u);
+        sum += e[d];
+    }
+    for (int d = 0; d < 4; ++d) lam[d] = e[d] / sum;
+}
+
+static int64_t sample_count(const orc_state *st, int64_t D)
+{
+    double S = (double)st->S;
+    double vol = (double)D / (6.0 * S * S * S);
+    int64_t n = (int64_t)floor(st->p.sampling_rate * vol + 0.5);
+    return n > ORC_MAX_SAMPLES ? ORC_MAX_SAMPLES : n;
+}
+
+static void eval_side_sampled(const orc_state *st, const orc_i3 own[4], const orc_i3 oth[4], int side,
+                              orc_tet *rec)
+{
+    const orc_problem *P = &st->p;
+    int64_t D = orient_arr(own);
+    if (D <= 0) return;                                /* folded copy: no samples */
+    const double *img_own = side == 0 ? P->img_s : P->img_t;
+    const double *img_oth = side == 0 ? P->img_t : P->img_s;
+    size_t N3 = (size_t)P->nx * P->ny * P->nz;
+    double S = (double)st->S;
+    double vo[4][3], vt[4][3];
+    for (int i = 0; i < 4; ++i) {
+        vo[i][0] = (double)own[i].x / S - 0.5; vo[i][1] = (double)own[i].y / S - 0.5; vo[i][2] = (double)own[i].z / S - 0.5;
+        vt[i][0] = (double)oth[i].x / S - 0.5; vt[i][1] = (double)oth[i].y / S - 0.5; vt[i][2] = (double)oth[i].z / S - 0.5;
+    }
+    uint32_t shift[4];
+    copy_shifts(own, shift);
+    int64_t n = sample_count(st, D);
+    double e_img = 0.0, e_guid = 0.0;
+    for (int64_t j = 0; j < n; ++j) {
+        double lam[4], p[3] = {0, 0, 0}, y[3] = {0, 0, 0};
+        sample_lambda(shift, (uint64_t)j, lam);
+        for (int i = 0; i < 4; ++i)
+            for (int a = 0; a < 3; ++a) {
+                p[a] += lam[i] * vo[i][a];
+                y[a] += lam[i] * vt[i][a];
+            }
+        double a = trilinear(img_own, P->nx, P->ny, P->nz, p);
+        double b = trilinear(img_oth, P->nx, P->ny, P->nz, y);
+        e_img += h_fn(P->h_mode, a, b);
+        if (P->g_mode == 0) {
+            for (int g = 0; g < st->G; ++g) {
+                double dg = trilinear(st->dist[side] + (size_t)g * N3, P->nx, P->ny, P->nz, p);
+                if (dg < st->r) {
+                    double dm = trilinear(st->dist[1 - side] + (size_t)g * N3, P->nx, P->ny, P->nz, y);
+                    e_guid += st->wgt[g] * (st->r - dg) / st->r * (dg - dm) * (dg - dm);
+                }
+            }
+        }
+    }
+    rec->e_img[side] = e_img;
+    rec->e_guid[side] += e_guid;
+    rec->n_vox[side] = n;
 }
 
 static double len3(double x, double y, double z)
@@ -539,6 +706,9 @@ int orc_setup(const orc_problem *P, orc_state **out)
     if ((int64_t)nmax * S > ((int64_t)1 << 16)) return ORC_EINVAL;
     if (P->n_points < 4 || P->n_tets < 1 || !P->tets || !P->ref_points) return ORC_EINVAL;
     if (P->h_mode < 0 || P->h_mode > 1 || P->g_mode < 0 || P->g_mode > 2) return ORC_EINVAL;
+    if (P->estimator < 0 || P->estimator > 1) return ORC_EINVAL;
+    if (P->estimator == 1 && (P->h_mode != 0 || !(P->sampling_rate > 0.0))) return ORC_EINVAL;
+    sobol_init();
     if (P->n_guid < 0 || (P->n_guid > 0 && (!P->guid_s || !P->guid_t))) return ORC_EINVAL;
     orc_state *st = (orc_state *)calloc(1, sizeof(orc_state));
     if (!st) return ORC_ENOMEM;
@@ -627,3 +797,15 @@ double orc_trilinear(const double *img, int nx, int ny, int nz, const double *y)
     return trilinear(img, nx, ny, nz, y);
 }
 double orc_h(int mode, double a, double b) { return h_fn(mode, a, b); }
+
+/* R13 building blocks */
+uint32_t orc_sobol(uint64_t j, int d) { sobol_init(); return (d >= 0 && d < 4) ? sobol_gray(j, d) : 0; }
+uint64_t orc_fnv1a64(const uint8_t *p, size_t n) { return fnv1a64(p, n); }
+uint64_t orc_splitmix64(uint64_t *state) { return splitmix64_next(state); }
+void orc_copy_shifts(const int64_t *tet12, uint32_t *shift)
+{
+    orc_i3 v[4];
+    for (int i = 0; i < 4; ++i) { v[i].x = tet12[3 * i]; v[i].y = tet12[3 * i + 1]; v[i].z = tet12[3 * i + 2]; }
+    copy_shifts(v, shift);
+}
+void orc_sample_lambda(const uint32_t *shift, uint64_t j, double *lam) { sobol_init(); sample_lambda(shift, j, lam); }

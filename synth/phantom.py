@@ -57,6 +57,8 @@ class Problem:
     g_mode: int = G_CONTINUOUS
     subvoxel_bits: int = 8
     lattice: Tuple[int, int, int] = (0, 0, 0)
+    estimator: int = 0              # 0: voxel association, 1: sampled points
+    sampling_rate: float = 1.0      # sampled estimator: points per voxel^3 of tet volume
 
     @property
     def n_points(self) -> int:
