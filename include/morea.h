@@ -78,6 +78,20 @@ typedef enum morea_gmode {
     MOREA_G_CONTINUOUS = 0, MOREA_G_PAIR_TRANSFER = 1, MOREA_G_OFF = 2
 } morea_gmode;
 
+/* Which points of a tet copy enter f_intensity and f_guidance.
+ * VOXELS: the voxel centres inside the copy, made exact by a symbolic
+ * perturbation (the association the paper's App. A.2 starts from, made
+ * watertight).  SAMPLED: the paper's own estimator (App. A.2): per copy
+ * N = floor(rate * volume + 1/2) points (capped at 2^24), uniform in
+ * barycentric coordinates from -log of a 4-D Sobol sequence (Gray-code
+ * order, Joe-Kuo direction numbers) whose 32-bit coordinates are XOR-shifted
+ * by values derived from the copy's snapped coordinates (FNV-1a over the 12
+ * coordinates as little-endian int32, then the first four splitmix64
+ * outputs, high 32 bits), so a copy always gets the same points; both
+ * images and the guidance maps are sampled trilinearly there.  SAMPLED
+ * requires h_mode PLAIN_SSD and g_mode CONTINUOUS or OFF. */
+typedef enum morea_estimator { MOREA_EST_VOXELS = 0, MOREA_EST_SAMPLED = 1 } morea_estimator;
+
 /* Bits of the device status word. */
 #define MOREA_DEV_BAD_POINT     0x1u   /* partial request names a point id out of range */
 #define MOREA_DEV_TOO_MANY      0x2u   /* partial request longer than max_changed / bad offsets */
@@ -111,6 +125,8 @@ typedef struct morea_problem_desc {
     int32_t max_solutions;         /* number of cache slots (solutions kept resident) >= 1 */
     int32_t max_requests;          /* largest n_req of morea_eval_partial (0: max_solutions) */
     int32_t max_changed;           /* largest changed-point count of one request (0: 64) */
+    int32_t estimator;             /* morea_estimator (0: VOXELS) */
+    float sampling_rate;           /* SAMPLED: points per voxel^3 of tet volume (<= 0: 1.0) */
 } morea_problem_desc;
 
 /* Per-(slot, tet) summands kept by the handle (what a partial evaluation

@@ -18,141 +18,11 @@
 // 16- or 8-byte load per z-plane of the other image's 2x2x2 neighbourhood
 // from its "quad" copy, and the band mask only in rows that touch a guidance
 // band.
-#include "morea_device.cuh"
+#include "image_ops.cuh"
 
 namespace morea {
 
 namespace {
-
-constexpr unsigned FULL = 0xffffffffu;
-
-template <typename TI>
-struct QuadOf;
-template <>
-struct QuadOf<float> {
-    using T = float4;
-};
-template <>
-struct QuadOf<__half> {
-    using T = uint2;
-};
-
-__device__ __forceinline__ float ld_img(const float *p, int idx) { return __ldg(p + idx); }
-__device__ __forceinline__ float ld_img(const __half *p, int idx) { return __half2float(__ldg(p + idx)); }
-
-// one z-plane of the neighbourhood: (x,y), (x+1,y), (x,y+1), (x+1,y+1)
-__device__ __forceinline__ void ld_quad(const float4 *q, int idx, float &a, float &b, float &c, float &d)
-{
-    const float4 v = __ldg(q + idx);
-    a = v.x;
-    b = v.y;
-    c = v.z;
-    d = v.w;
-}
-
-__device__ __forceinline__ void ld_quad(const uint2 *q, int idx, float &a, float &b, float &c, float &d)
-{
-    const uint2 v = __ldg(q + idx);
-    const float2 lo = __half22float2(*reinterpret_cast<const __half2 *>(&v.x));
-    const float2 hi = __half22float2(*reinterpret_cast<const __half2 *>(&v.y));
-    a = lo.x;
-    b = lo.y;
-    c = hi.x;
-    d = hi.y;
-}
-
-// Trilinear sample with the position clamped to [0, n-1] per axis and the
-// cell i0 = min(floor(y), n - 2), from the quad copy of the image.
-template <typename QT>
-__device__ __forceinline__ float trilin_quad(const QT *q, int nx, int ny, int nz, float yx, float yy, float yz)
-{
-    const float cx = fminf(fmaxf(yx, 0.0f), (float)(nx - 1));
-    const float cy = fminf(fmaxf(yy, 0.0f), (float)(ny - 1));
-    const float cz = fminf(fmaxf(yz, 0.0f), (float)(nz - 1));
-    const int ix = min((int)cx, nx - 2), iy = min((int)cy, ny - 2), iz = min((int)cz, nz - 2);
-    const float fx = cx - (float)ix, fy = cy - (float)iy, fz = cz - (float)iz;
-    const int b = (iz * ny + iy) * nx + ix;
-    float v000, v100, v010, v110, v001, v101, v011, v111;
-    ld_quad(q, b, v000, v100, v010, v110);
-    ld_quad(q, b + nx * ny, v001, v101, v011, v111);
-    const float c00 = fmaf(fx, v100 - v000, v000), c10 = fmaf(fx, v110 - v010, v010);
-    const float c01 = fmaf(fx, v101 - v001, v001), c11 = fmaf(fx, v111 - v011, v011);
-    const float c0 = fmaf(fy, c10 - c00, c00), c1 = fmaf(fy, c11 - c01, c01);
-    return fmaf(fz, c1 - c0, c0);
-}
-
-// The same sample when the position is known to lie strictly inside
-// [0, n-1] per axis: the clamps and the last-cell guard are no-ops there.
-template <typename QT>
-__device__ __forceinline__ float trilin_quad_inner(const QT *q, int nx, int ny, float yx, float yy, float yz)
-{
-    const int ix = (int)yx, iy = (int)yy, iz = (int)yz;
-    const float fx = yx - (float)ix, fy = yy - (float)iy, fz = yz - (float)iz;
-    const int b = (iz * ny + iy) * nx + ix;
-    float v000, v100, v010, v110, v001, v101, v011, v111;
-    ld_quad(q, b, v000, v100, v010, v110);
-    ld_quad(q, b + nx * ny, v001, v101, v011, v111);
-    const float c00 = fmaf(fx, v100 - v000, v000), c10 = fmaf(fx, v110 - v010, v010);
-    const float c01 = fmaf(fx, v101 - v001, v001), c11 = fmaf(fx, v111 - v011, v011);
-    const float c0 = fmaf(fy, c10 - c00, c00), c1 = fmaf(fy, c11 - c01, c01);
-    return fmaf(fz, c1 - c0, c0);
-}
-
-// The same sample from a plain FP32 image (guidance distance maps).
-__device__ __forceinline__ float trilin_plain(const float *img, int nx, int ny, int nz, float yx, float yy, float yz)
-{
-    const float cx = fminf(fmaxf(yx, 0.0f), (float)(nx - 1));
-    const float cy = fminf(fmaxf(yy, 0.0f), (float)(ny - 1));
-    const float cz = fminf(fmaxf(yz, 0.0f), (float)(nz - 1));
-    const int ix = min((int)cx, nx - 2), iy = min((int)cy, ny - 2), iz = min((int)cz, nz - 2);
-    const float fx = cx - (float)ix, fy = cy - (float)iy, fz = cz - (float)iz;
-    const int sy = nx, sz = nx * ny;
-    const int b = (iz * ny + iy) * nx + ix;
-    const float v000 = __ldg(img + b), v100 = __ldg(img + b + 1);
-    const float v010 = __ldg(img + b + sy), v110 = __ldg(img + b + sy + 1);
-    const float v001 = __ldg(img + b + sz), v101 = __ldg(img + b + sz + 1);
-    const float v011 = __ldg(img + b + sz + sy), v111 = __ldg(img + b + sz + sy + 1);
-    const float c00 = fmaf(fx, v100 - v000, v000), c10 = fmaf(fx, v110 - v010, v010);
-    const float c01 = fmaf(fx, v101 - v001, v001), c11 = fmaf(fx, v111 - v011, v011);
-    const float c0 = fmaf(fy, c10 - c00, c00), c1 = fmaf(fy, c11 - c01, c01);
-    return fmaf(fz, c1 - c0, c0);
-}
-
-template <int HMODE>
-__device__ __forceinline__ float hfun(float a, float b)
-{
-    const float d = a - b;
-    if (HMODE == MOREA_H_PLAIN_SSD) return d * d;
-    if (a > 0.0f && b > 0.0f) return d * d;
-    if (a == 0.0f && b == 0.0f) return 0.0f;
-    return 1.0f;
-}
-
-// Kahan-compensated accumulation; (s, c) holds s - c.
-__device__ __forceinline__ void kadd(float &s, float &c, float x)
-{
-    const float y = __fsub_rn(x, c);
-    const float t = __fadd_rn(s, y);
-    c = __fsub_rn(__fsub_rn(t, s), y);
-    s = t;
-}
-
-// Warp reduction of compensated pairs (hi, lo): error-free two-sum of the
-// high parts, low parts and errors summed separately.
-__device__ __forceinline__ float warp_comp_sum(float hi, float lo)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float h2 = __shfl_xor_sync(FULL, hi, o);
-        const float l2 = __shfl_xor_sync(FULL, lo, o);
-        const float s = __fadd_rn(hi, h2);
-        const float bp = __fsub_rn(s, hi);
-        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(h2, bp));
-        hi = s;
-        lo = __fadd_rn(__fadd_rn(lo, l2), err);
-    }
-    return __fadd_rn(hi, lo);
-}
 
 // Smallest i in [ilo, ihi + 1] with A i + B > 0 (A > 0); ihi + 1 if none.
 __device__ __forceinline__ int face_lo(long long A, long long B, float est, int ilo, int ihi)
@@ -306,29 +176,6 @@ __device__ __noinline__ void guidance_pairs(const DevProblem &P, const RasterSet
                     }
                 }
             }
-}
-
-// Item scheduling of the image and guidance passes: static striding of the
-// (entry, side) items over all warps, or (chunk > 0) a work queue from which
-// each warp takes `chunk` consecutive items with one atomic add, so warps that
-// drew large tets do not hold up the tail of an uneven batch.
-template <typename F>
-__device__ __forceinline__ void run_items(int n_items, int chunk, int *queue, F &&body)
-{
-    const int lane = threadIdx.x & 31;
-    if (chunk <= 0) {
-        const int wpb = blockDim.x >> 5;
-        for (int item = blockIdx.x * wpb + (threadIdx.x >> 5); item < n_items; item += gridDim.x * wpb) body(item);
-        return;
-    }
-    for (;;) {
-        int base = 0;
-        if (lane == 0) base = atomicAdd(queue, chunk);
-        base = __shfl_sync(FULL, base, 0);
-        if (base >= n_items) break;
-        const int end = min(base + chunk, n_items);
-        for (int item = base; item < end; ++item) body(item);
-    }
 }
 
 // Pass modes of the image kernel.
@@ -725,6 +572,8 @@ cudaError_t launch_raster(const DevProblem *probs, const DevProblem &hp, const W
     if (grid <= 0) grid = sm_count() * 8;
     cudaError_t e = cudaMemsetAsync(queue, 0, kQueueList * sizeof(int), st);
     if (e != cudaSuccess) return e;
+    if (hp.estimator == MOREA_EST_SAMPLED)
+        return launch_sample(probs, hp, entries, setup, rout, n_entries_dev, n_entries_host, grid, chunk, queue, st);
     if (hp.dtype == MOREA_F16) {
         if (hp.h_mode == MOREA_H_MOREA_FG)
             return launch_g<__half, MOREA_H_MOREA_FG>(probs, hp.g_mode, entries, setup, rout, bandrows, n_entries_dev,

@@ -105,6 +105,11 @@ morea_status morea_create_problem(const morea_problem_desc *d, void *stream, mor
     if (d->n_points < 4 || d->n_tets < 1 || !d->tets || !d->ref_points) return MOREA_EINVAL;
     if (d->h_mode != MOREA_H_PLAIN_SSD && d->h_mode != MOREA_H_MOREA_FG) return MOREA_EINVAL;
     if (d->g_mode < MOREA_G_CONTINUOUS || d->g_mode > MOREA_G_OFF) return MOREA_EINVAL;
+    if (d->estimator != MOREA_EST_VOXELS && d->estimator != MOREA_EST_SAMPLED) return MOREA_EINVAL;
+    if (d->estimator == MOREA_EST_SAMPLED &&
+        (d->h_mode != MOREA_H_PLAIN_SSD || d->g_mode == MOREA_G_PAIR_TRANSFER || std::isnan(d->sampling_rate) ||
+         d->sampling_rate > 1.0e6f))
+        return MOREA_EINVAL;
     if (d->n_guid < 0 || (d->n_guid > 0 && (!d->guid_s || !d->guid_t))) return MOREA_EINVAL;
     if (std::isnan(d->trunc_radius)) return MOREA_EINVAL;
     if (d->max_solutions < 1 || d->max_requests < 0 || d->max_changed < 0 || d->max_changed > 1024)
@@ -247,6 +252,8 @@ morea_status morea_create_problem(const morea_problem_desc *d, void *stream, mor
     hp.H = H;
     hp.h_mode = d->h_mode;
     hp.g_mode = d->g_mode;
+    hp.estimator = d->estimator;
+    hp.rate = d->sampling_rate > 0.0f ? d->sampling_rate : 1.0f;
     hp.G = G;
     hp.n_points = V;
     hp.n_tets = T;
@@ -274,6 +281,9 @@ morea_status morea_create_problem(const morea_problem_desc *d, void *stream, mor
     morea_totals *totals = nullptr;
     unsigned *status = nullptr;
     const bool continuous = d->g_mode == MOREA_G_CONTINUOUS;
+    const bool sampled = d->estimator == MOREA_EST_SAMPLED;
+    const bool banded = continuous && !sampled;          // band rows and their lists (voxel estimator)
+    uint8_t *bandd[2] = {nullptr, nullptr};
 #define TRY(x)                                                                                     \
     do {                                                                                           \
         e = (x);                                                                                   \
@@ -297,8 +307,9 @@ morea_status morea_create_problem(const morea_problem_desc *d, void *stream, mor
         TRY(dalloc(p, &quad[s], (size_t)N * esz * 4));
         if (continuous) {
             TRY(dalloc(p, &band[s], (size_t)N));
-            TRY(dalloc(p, &bandrow[s], (size_t)ny * nz));
+            if (banded) TRY(dalloc(p, &bandrow[s], (size_t)ny * nz));
             if (G > 0) TRY(dalloc(p, &dmap[s], (size_t)N * G));
+            if (sampled && G > 0) TRY(dalloc(p, &bandd[s], (size_t)N));
         }
     }
     TRY(dalloc(p, &goff_d, goff.size()));
@@ -310,7 +321,7 @@ morea_status morea_create_problem(const morea_problem_desc *d, void *stream, mor
     TRY(dalloc(p, &p->entries, (size_t)cap));
     TRY(dalloc(p, &p->setup, 2 * (size_t)cap));
     TRY(dalloc(p, &p->rout, 2 * (size_t)cap));
-    if (continuous) TRY(dalloc(p, &p->bandrows, 2 * (size_t)cap * kBandRowsPerItem));
+    if (banded) TRY(dalloc(p, &p->bandrows, 2 * (size_t)cap * kBandRowsPerItem));
     TRY(dalloc(p, &p->tout, (size_t)cap));
     TRY(dalloc(p, &p->counter, 1));
     TRY(dalloc(p, &p->rinfo, (size_t)max_req));
@@ -319,7 +330,7 @@ morea_status morea_create_problem(const morea_problem_desc *d, void *stream, mor
     TRY(dalloc(p, &p->req_chg_q, 2 * (size_t)max_req * max_changed));
     TRY(dalloc(p, &p->dp, 1));
     TRY(dalloc(p, &p->visits, 1));
-    TRY(dalloc(p, &p->queue, queue_ints(cap, continuous)));
+    TRY(dalloc(p, &p->queue, queue_ints(cap, banded)));
 
     hp.img[0] = img[0];
     hp.img[1] = img[1];
@@ -331,6 +342,8 @@ morea_status morea_create_problem(const morea_problem_desc *d, void *stream, mor
     hp.quad[1] = quad[1];
     hp.bandrow[0] = bandrow[0];
     hp.bandrow[1] = bandrow[1];
+    hp.bandd[0] = bandd[0];
+    hp.bandd[1] = bandd[1];
     hp.tets = dtets;
     hp.cdelta = dcd;
     for (int s = 0; s < 2; ++s) {
@@ -378,9 +391,11 @@ morea_status morea_create_problem(const morea_problem_desc *d, void *stream, mor
                                 cudaMemcpyHostToDevice, st));
             TRY(launch_distance_maps(hp, gsort_d, goff_d, dmap[s], band[s], st));
             TRY(cudaStreamSynchronize(st));   // gsort_d is reused for the other side
+            if (sampled) TRY(launch_band_dilate(hp, band[s], bandd[s], st));
         }
     }
-    if (continuous) {
+    if (sampled) TRY(sample_setup(st));
+    if (banded) {
         for (int s = 0; s < 2; ++s) TRY(launch_band_rows(hp, s, bandrow[s], st));
         // per-row sorted lists of band voxels (built on the host from the masks)
         std::vector<uint8_t> hband((size_t)N);

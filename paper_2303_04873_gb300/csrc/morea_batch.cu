@@ -118,7 +118,7 @@ morea_status morea_batch_create(morea_problem *const *problems, int32_t n_proble
     for (int i = 0; i < n_problems; ++i) {
         const morea_problem *p = problems[i];
         if (!p || p->device != p0->device || p->hp.dtype != p0->hp.dtype || p->hp.h_mode != p0->hp.h_mode ||
-            p->hp.g_mode != p0->hp.g_mode)
+            p->hp.g_mode != p0->hp.g_mode || p->hp.estimator != p0->hp.estimator)
             return MOREA_EINVAL;
         for (int j = 0; j < i; ++j)
             if (problems[j] == p) return MOREA_EINVAL;
@@ -139,9 +139,11 @@ morea_status morea_batch_create(morea_problem *const *problems, int32_t n_proble
     if (e == cudaSuccess) e = dalloc(b, &b->setup, 2 * (size_t)cap);
     if (e == cudaSuccess) e = dalloc(b, &b->rout, 2 * (size_t)cap);
     if (e == cudaSuccess) e = dalloc(b, &b->tout, (size_t)cap);
-    if (e == cudaSuccess && p0->hp.g_mode == MOREA_G_CONTINUOUS)
+    if (e == cudaSuccess && p0->hp.g_mode == MOREA_G_CONTINUOUS && p0->hp.estimator == MOREA_EST_VOXELS)
         e = dalloc(b, &b->bandrows, 2 * (size_t)cap * kBandRowsPerItem);
-    if (e == cudaSuccess) e = dalloc(b, &b->queue, queue_ints(cap, p0->hp.g_mode == MOREA_G_CONTINUOUS));
+    if (e == cudaSuccess)
+        e = dalloc(b, &b->queue,
+                   queue_ints(cap, p0->hp.g_mode == MOREA_G_CONTINUOUS && p0->hp.estimator == MOREA_EST_VOXELS));
     if (e == cudaSuccess)
         e = cudaMemcpy(b->dprobs, hps.data(), sizeof(DevProblem) * n_problems, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {

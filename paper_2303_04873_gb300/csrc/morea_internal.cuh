@@ -20,6 +20,8 @@ constexpr int kBlock = 256;
 struct DevProblem {
     int nx, ny, nz, dtype;
     int kbits, S, H, h_mode;
+    int estimator;                   // morea_estimator
+    float rate;                      // sampled estimator: points per voxel^3
     int g_mode, G, n_points, n_tets;
     float r, inv_r;
     int n_guid, cshift;
@@ -32,6 +34,7 @@ struct DevProblem {
     const int *band_start[2];        // [nz*ny + 1] CSR of the band voxels of each image row
     const short *band_x[2];          // their x, ascending within a row
     const short *band_rank[2];       // [N] band voxels before x in the same image row
+    const uint8_t *bandd[2];         // [N] band bits OR-ed over the 2x2x2 cell at each voxel (sampled)
     const int4 *tets;                // positively oriented topology
     const float *cdelta;             // elasticity factor per tet
     const int4 *gq[2];               // snapped guidance points per side
@@ -151,6 +154,13 @@ inline size_t queue_ints(long long cap_entries, bool continuous)
 {
     return kQueueList + (continuous ? 2 * (size_t)cap_entries : 0);
 }
+// The sampled estimator (k_sample.cu): Sobol direction numbers into constant
+// memory (once per device), the dilated band masks, and the image pass.
+cudaError_t sample_setup(cudaStream_t st);
+cudaError_t launch_band_dilate(const DevProblem &hp, const uint8_t *band, uint8_t *out, cudaStream_t st);
+cudaError_t launch_sample(const DevProblem *probs, const DevProblem &hp, const WorkEntry *entries,
+                          const RasterSetup *setup, RasterOut *rout, const int *n_entries_dev, int n_entries_host,
+                          int grid, int chunk, int *queue, cudaStream_t st);
 cudaError_t launch_raster(const DevProblem *probs, const DevProblem &hp, const WorkEntry *entries,
                           const RasterSetup *setup, RasterOut *rout, int2 *bandrows, const int *n_entries_dev,
                           int n_entries_host, int grid, int chunk, int *queue, cudaStream_t st);

@@ -73,6 +73,7 @@ class ProblemDesc(ctypes.Structure):
         ("trunc_radius", ctypes.c_double), ("h_mode", ctypes.c_int32), ("g_mode", ctypes.c_int32),
         ("subvoxel_bits", ctypes.c_int32), ("max_solutions", ctypes.c_int32),
         ("max_requests", ctypes.c_int32), ("max_changed", ctypes.c_int32),
+        ("estimator", ctypes.c_int32), ("sampling_rate", ctypes.c_float),
     ]
 
 
@@ -177,6 +178,7 @@ class Problem:
     def __init__(self, prob, max_solutions: Optional[int] = None, max_requests: int = 0,
                  max_changed: int = 64, stream=None, **override):
         g = lambda name: override.get(name, getattr(prob, name))
+        g_opt = lambda name, default: override.get(name, getattr(prob, name, default))
         L = lib()
         keep = []
 
@@ -217,7 +219,8 @@ class Problem:
             n_guid=n_guid, guid_s=ptr(gs), guid_t=ptr(gt), guid_group=ptr(gg),
             trunc_radius=float(g("trunc_radius")), h_mode=int(g("h_mode")), g_mode=int(g("g_mode")),
             subvoxel_bits=int(g("subvoxel_bits")), max_solutions=int(max_solutions),
-            max_requests=int(max_requests), max_changed=int(max_changed))
+            max_requests=int(max_requests), max_changed=int(max_changed),
+            estimator=int(g_opt("estimator", 0)), sampling_rate=float(g_opt("sampling_rate", 1.0)))
         h = ctypes.c_void_p()
         _check(L.morea_create_problem(ctypes.byref(desc), _stream(stream), ctypes.byref(h)),
                "morea_create_problem")
@@ -235,6 +238,7 @@ class Problem:
         self.max_requests = int(max_requests) if max_requests else int(max_solutions)
         self.max_changed = int(max_changed)
         self.h_mode, self.g_mode = int(g("h_mode")), int(g("g_mode"))
+        self.estimator = int(g_opt("estimator", 0))
 
     # -- lifetime -----------------------------------------------------------
     def close(self):

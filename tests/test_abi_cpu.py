@@ -60,6 +60,7 @@ int main(void) {
   P(morea_problem_desc, image_s) P(morea_problem_desc, n_points) P(morea_problem_desc, tets)
   P(morea_problem_desc, n_labels) P(morea_problem_desc, guid_s) P(morea_problem_desc, trunc_radius)
   P(morea_problem_desc, h_mode) P(morea_problem_desc, max_changed)
+  P(morea_problem_desc, estimator) P(morea_problem_desc, sampling_rate)
   P(morea_tet_record, n_vox) P(morea_tet_record, e_mag) P(morea_tet_record, sev)
   P(morea_totals, n_vox) P(morea_totals, sev)
   return 0;
@@ -107,6 +108,8 @@ def _desc(mo, **kw):
     dict(nx=1), dict(dtype=7), dict(n_points=3), dict(h_mode=5), dict(g_mode=9), dict(subvoxel_bits=12),
     dict(subvoxel_bits=1), dict(max_solutions=0), dict(max_changed=5000), dict(n_labels=0),
     dict(trunc_radius=float("nan")), dict(image_s=None),
+    dict(estimator=2), dict(estimator=1, h_mode=1), dict(estimator=1, g_mode=1),
+    dict(estimator=1, sampling_rate=float("nan")), dict(estimator=1, sampling_rate=1e9),
 ])
 def test_invalid_descriptions_rejected_on_host(mo, bad):
     d, keep = _desc(mo, **bad)
