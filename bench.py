@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--rounds", type=int, default=4, help="c3: mixing rounds per generation")
     ap.add_argument("--epochs", type=int, default=20, help="c3: surrogate training epochs")
     ap.add_argument("--seeds", type=int, default=5, help="c3: EA seeds compared (200, 201, ...)")
+    ap.add_argument("--estimator", choices=["voxels", "sampled"], default="voxels",
+                    help="c1/c2: voxel centres (default) or the sampled estimator of App. A.2 (1 point per voxel^3)")
     ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4"], default="c1",
                     help="c1: 128x128x96 f32 (the headline); c2: 256x256x160 f16 graded mesh; "
                          "c4: 16 uneven f16 problems in one batched graph launch")
@@ -68,9 +70,12 @@ WORKLOADS = {
 }
 
 
-def workload(seed_offset=0, name="c1"):
+def workload(seed_offset=0, name="c1", estimator="voxels"):
+    import dataclasses
     import synth
     p = synth.make_c1() if name == "c1" else synth.make_c2()
+    if estimator == "sampled":
+        p = dataclasses.replace(p, estimator=1, sampling_rate=1.0)
     adj = synth.vertex_adjacency(p.tets, p.n_points)
     rounds = synth.partial_requests(p, adj, ROUNDS, 4, 32, 1.0, 3 + seed_offset)
     rng = np.random.default_rng(4 + seed_offset)
@@ -197,7 +202,7 @@ def run_reference(args):
         return 0
     import oracle
     cores = os.cpu_count() or 1
-    p, rounds, accept = workload(name=args.workload)
+    p, rounds, accept = workload(name=args.workload, estimator=args.estimator)
     orc = oracle.Oracle(p)
     per_step = []
     desc = ""
@@ -212,7 +217,7 @@ def run_reference(args):
         "impl": "reference", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": evals / value * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.workload][0], "l2": "n/a (CPU)"},
+        "config": {"workload": WORKLOADS[args.workload][0], "estimator": args.estimator, "l2": "n/a (CPU)"},
         "cpu_baseline": {"value": value, "unit": "solution-evals/s", "cores": cores, "kind": "oracle",
                          "sample": desc},
         "e2e": {"value": value, "unit": "solution-evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -281,7 +286,7 @@ def run_ours(args):
     from paper_2303_04873_gb300 import morea
 
     # the oracle sample runs first, on host threads, before any GPU work
-    p, rounds, accept = workload(name=args.workload)
+    p, rounds, accept = workload(name=args.workload, estimator=args.estimator)
     bytes_per_visit = 2 * WORKLOADS[args.workload][1]
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -420,16 +425,20 @@ def run_ours(args):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.workload][0],
+        "config": {"workload": WORKLOADS[args.workload][0], "estimator": args.estimator,
                    "evals_per_step": evals_per_step, "l2": "flushed before every timed step (512 MiB write)",
                    "launch": {"blocks_per_sm": bps, "chunk": chunk},
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": measured_traffic(args.workload),
+                     "frac": achieved / peak,
+                     "traffic": measured_traffic(args.workload) if args.estimator == "voxels" else None,
                      "traffic_unit": "bytes per launch (ncu, DRAM read + write)",
-                     "kernel": "image pass: k_raster (rasterise + map + trilinear + h) + k_guidance",
+                     "kernel": ("image pass: k_raster (rasterise + map + trilinear + h) + k_guidance"
+                                if args.estimator == "voxels" else
+                                "image pass: k_sample (Sobol points + map + 2 trilinear samples + h + guidance)"),
                      "peak_kind": f"{peak_kind} copy bandwidth",
-                     "algorithmic_bytes": f"{bytes_per_visit} B per voxel visit x {visits_per_step} visits/step",
+                     "algorithmic_bytes": f"{bytes_per_visit} B per visit (voxel or sample point) x "
+                                          f"{visits_per_step} visits/step",
                      "kernel_ms_per_step": raster_ms / args.steps, "launches": raster_launches},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "solution-evals/s", "h2d_bytes_per_step": int(h2d),

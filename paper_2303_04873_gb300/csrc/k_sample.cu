@@ -70,6 +70,10 @@ __global__ void __launch_bounds__(kBlock, 4) k_sample(const DevProblem *__restri
                                                      int n_entries_host, int chunk, int *queue)
 {
     using QT = typename QuadOf<TI>::T;
+    // per warp: vertex 0 and edge vectors of the own (0..3) and the other
+    // copy (4..7), voxel units, read by every sample from shared memory
+    __shared__ float4 geo[kBlock / 32][8];
+    float4 *G4 = geo[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     const int n_ent = n_entries_dev ? min(*n_entries_dev, n_entries_host) : n_entries_host;
     run_items(2 * n_ent, chunk, queue + kQueueRaster, [&](const int item) {
@@ -82,8 +86,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_sample(const DevProblem *__restri
             const WorkEntry &we = entries[e];
             const DevProblem &P = probs[we.prob];
             const int4 *own = we.q[side], *oth = we.q[1 - side];
-            const int4 q0 = own[0], q1 = own[1], q2 = own[2], q3 = own[3];
-            const double D = orient_d(q0, q1, q2, q3);
+            const double D = orient_d(own[0], own[1], own[2], own[3]);
             const double Sd = (double)P.S;
             const double vol = D / (6.0 * Sd * Sd * Sd);
             n = (long long)floor((double)P.rate * vol + 0.5);
@@ -91,16 +94,15 @@ __global__ void __launch_bounds__(kBlock, 4) k_sample(const DevProblem *__restri
             uint32_t shift[4];
             copy_shifts(own, shift);
             // vertex 0 and edges of both copies in voxel units (exact in FP32)
-            const float inv_s = 1.0f / (float)P.S, off = 0.5f;
-            const float v0x = q0.x * inv_s - off, v0y = q0.y * inv_s - off, v0z = q0.z * inv_s - off;
-            const float e1x = (q1.x - q0.x) * inv_s, e1y = (q1.y - q0.y) * inv_s, e1z = (q1.z - q0.z) * inv_s;
-            const float e2x = (q2.x - q0.x) * inv_s, e2y = (q2.y - q0.y) * inv_s, e2z = (q2.z - q0.z) * inv_s;
-            const float e3x = (q3.x - q0.x) * inv_s, e3y = (q3.y - q0.y) * inv_s, e3z = (q3.z - q0.z) * inv_s;
-            const int4 r0 = oth[0], r1 = oth[1], r2 = oth[2], r3 = oth[3];
-            const float w0x = r0.x * inv_s - off, w0y = r0.y * inv_s - off, w0z = r0.z * inv_s - off;
-            const float f1x = (r1.x - r0.x) * inv_s, f1y = (r1.y - r0.y) * inv_s, f1z = (r1.z - r0.z) * inv_s;
-            const float f2x = (r2.x - r0.x) * inv_s, f2y = (r2.y - r0.y) * inv_s, f2z = (r2.z - r0.z) * inv_s;
-            const float f3x = (r3.x - r0.x) * inv_s, f3y = (r3.y - r0.y) * inv_s, f3z = (r3.z - r0.z) * inv_s;
+            if (lane < 8) {
+                const int4 *c = lane < 4 ? own : oth;
+                const int i = lane & 3;
+                const float inv_s = 1.0f / (float)P.S;
+                const int4 a = c[i], o = c[0];
+                G4[lane] = i == 0 ? make_float4(a.x * inv_s - 0.5f, a.y * inv_s - 0.5f, a.z * inv_s - 0.5f, 0.0f)
+                                  : make_float4((a.x - o.x) * inv_s, (a.y - o.y) * inv_s, (a.z - o.z) * inv_s, 0.0f);
+            }
+            __syncwarp();
             const int nx = P.nx, ny = P.ny, nz = P.nz;
             const QT *qown = (const QT *)P.quad[side];
             const QT *qoth = (const QT *)P.quad[1 - side];
@@ -126,12 +128,14 @@ __global__ void __launch_bounds__(kBlock, 4) k_sample(const DevProblem *__restri
                     }
                     const float inv = 1.0f / sum;
                     const float l1 = ed[1] * inv, l2 = ed[2] * inv, l3 = ed[3] * inv;
-                    const float px = fmaf(l3, e3x, fmaf(l2, e2x, fmaf(l1, e1x, v0x)));
-                    const float py = fmaf(l3, e3y, fmaf(l2, e2y, fmaf(l1, e1y, v0y)));
-                    const float pz = fmaf(l3, e3z, fmaf(l2, e2z, fmaf(l1, e1z, v0z)));
-                    const float yx = fmaf(l3, f3x, fmaf(l2, f2x, fmaf(l1, f1x, w0x)));
-                    const float yy = fmaf(l3, f3y, fmaf(l2, f2y, fmaf(l1, f1y, w0y)));
-                    const float yz = fmaf(l3, f3z, fmaf(l2, f2z, fmaf(l1, f1z, w0z)));
+                    const float4 v0 = G4[0], e1 = G4[1], e2 = G4[2], e3 = G4[3];
+                    const float px = fmaf(l3, e3.x, fmaf(l2, e2.x, fmaf(l1, e1.x, v0.x)));
+                    const float py = fmaf(l3, e3.y, fmaf(l2, e2.y, fmaf(l1, e1.y, v0.y)));
+                    const float pz = fmaf(l3, e3.z, fmaf(l2, e2.z, fmaf(l1, e1.z, v0.z)));
+                    const float4 w0 = G4[4], f1 = G4[5], f2 = G4[6], f3 = G4[7];
+                    const float yx = fmaf(l3, f3.x, fmaf(l2, f2.x, fmaf(l1, f1.x, w0.x)));
+                    const float yy = fmaf(l3, f3.y, fmaf(l2, f2.y, fmaf(l1, f1.y, w0.y)));
+                    const float yz = fmaf(l3, f3.z, fmaf(l2, f2.z, fmaf(l1, f1.z, w0.z)));
                     const float a = trilin_quad(qown, nx, ny, nz, px, py, pz);
                     const float b = trilin_quad(qoth, nx, ny, nz, yx, yy, yz);
                     kadd(s_img, c_img, (a - b) * (a - b));
