@@ -71,7 +71,8 @@ def build(force: bool = False) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-std=c99", "-O2", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _SRC,
+                               "-lm"])
         os.replace(tmp, _SO)
     return _SO
 
@@ -119,6 +120,11 @@ def lib():
         L.orc_splitmix64.restype = ctypes.c_uint64
         L.orc_copy_shifts.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
         L.orc_sample_lambda.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]
+        L.orc_repair.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                 ctypes.c_double, ctypes.POINTER(ctypes.c_uint64)]
+        L.orc_repair.restype = ctypes.c_int
+        L.orc_repair_sigma.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double]
+        L.orc_repair_sigma.restype = ctypes.c_double
         _lib = L
     return _lib
 
@@ -237,6 +243,24 @@ class Oracle:
         rec = np.zeros(1, TET_DTYPE)
         self._L.orc_eval_tet(self._h, _ptr(src), _ptr(tgt), int(t), _ptr(rec))
         return rec[0]
+
+    def repair(self, src, tgt, noise, max_points: int, scale: float = 1.0):
+        """Repair (R14) of one solution; returns (src, tgt, moved, severity)."""
+        s = np.array(src, dtype=np.float32, copy=True, order="C")
+        t = np.array(tgt, dtype=np.float32, copy=True, order="C")
+        z = np.ascontiguousarray(noise, dtype=np.float32)
+        assert z.size >= max_points * 64 * 3
+        sev = ctypes.c_uint64(0)
+        moved = self._L.orc_repair(self._h, _ptr(s), _ptr(t), _ptr(z), int(max_points), float(scale),
+                                   ctypes.byref(sev))
+        if moved < 0:
+            raise OracleError("oracle repair failed")
+        S = float(1 << int(self._P.subvoxel_bits))
+        return s, t, int(moved), sev.value / (6.0 * S * S * S)
+
+    def repair_sigma(self, X, v: int, scale: float = 1.0) -> float:
+        x = np.ascontiguousarray(X, dtype=np.float32)
+        return float(self._L.orc_repair_sigma(self._h, _ptr(x), int(v), float(scale)))
 
     def eval_partial(self, old_src, old_tgt, new_src, new_tgt, changed, old_result):
         arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in (old_src, old_tgt, new_src, new_tgt)]

@@ -70,6 +70,19 @@
  *      images are sampled trilinearly (R4), and h, the guidance term (own
  *      map sampled at p) and the counts (N per copy) enter as in the voxel
  *      estimator.  Only h_mode PLAIN_SSD.
+ *   R14 repair (Sec. 4.3.1).  Source mesh first, then target mesh; within a
+ *      mesh the tets are visited in order and, if folded at that moment,
+ *      their four vertices in order, each vertex at most once per mesh.  A
+ *      vertex v at float position x gets sigma = scale * (the smallest
+ *      distance, over the tets of its star, from v to the plane of the face
+ *      opposite v), at least 1/2^k voxel; trial k (k = 0..63) is
+ *      x + sigma z_k rounded to float, z_k the caller's standard normal
+ *      draws for this (solution, visit, trial).  The trial with the largest
+ *      strictly positive decrease of the star's severity (sum of |orient|
+ *      over its folded tets; ties to the lowest k) replaces x; if no trial
+ *      decreases it, the repair of the solution stops.  At most max_points
+ *      visits per solution.  FP64 without contraction, so the float trial
+ *      positions are the same on every machine.
  */
 #include <math.h>
 #include <stdint.h>
@@ -809,3 +822,134 @@ void orc_copy_shifts(const int64_t *tet12, uint32_t *shift)
     copy_shifts(v, shift);
 }
 void orc_sample_lambda(const uint32_t *shift, uint64_t j, double *lam) { sobol_init(); sample_lambda(shift, j, lam); }
+
+/* ------------------------------------------------------------------ */
+/* R14: repair of folded solutions (Sec. 4.3.1)                        */
+/* ------------------------------------------------------------------ */
+
+static orc_i3 vertex_at(const orc_state *st, const float *X, int v) { return snap3(st, X + 3 * (size_t)v); }
+
+/* sum of |orient| over the folded tets of v's star, v placed at q */
+static uint64_t star_severity(const orc_state *st, const float *X, int v, orc_i3 q)
+{
+    uint64_t sev = 0;
+    for (int t = 0; t < st->p.n_tets; ++t) {
+        const int32_t *tv = st->tets + 4 * t;
+        if (tv[0] != v && tv[1] != v && tv[2] != v && tv[3] != v) continue;
+        orc_i3 c[4];
+        for (int i = 0; i < 4; ++i) c[i] = tv[i] == v ? q : vertex_at(st, X, tv[i]);
+        int64_t D = orient_arr(c);
+        if (D <= 0) sev += (uint64_t)(D < 0 ? -D : D);
+    }
+    return sev;
+}
+
+/* distance (voxels) from p to the plane through a, b, c; infinity if degenerate */
+static double plane_distance(const orc_state *st, orc_i3 p, orc_i3 a, orc_i3 b, orc_i3 c)
+{
+    int64_t ux = b.x - a.x, uy = b.y - a.y, uz = b.z - a.z;
+    int64_t vx = c.x - a.x, vy = c.y - a.y, vz = c.z - a.z;
+    int64_t nx = uy * vz - uz * vy, ny = uz * vx - ux * vz, nz = ux * vy - uy * vx;
+    double nn = (double)nx * (double)nx + (double)ny * (double)ny + (double)nz * (double)nz;
+    if (nn == 0.0) return INFINITY;
+    int64_t num = nx * (p.x - a.x) + ny * (p.y - a.y) + nz * (p.z - a.z);
+    double d = fabs((double)num) / sqrt(nn);
+    return d / (double)st->S;
+}
+
+static double repair_sigma(const orc_state *st, const float *X, int v, double scale)
+{
+    orc_i3 p = vertex_at(st, X, v);
+    double dmin = INFINITY;
+    for (int t = 0; t < st->p.n_tets; ++t) {
+        const int32_t *tv = st->tets + 4 * t;
+        orc_i3 f[3];
+        int n = 0, has = 0;
+        for (int i = 0; i < 4; ++i) {
+            if (tv[i] == v) has = 1;
+            else if (n < 3) f[n++] = vertex_at(st, X, tv[i]);
+        }
+        if (!has || n != 3) continue;
+        double d = plane_distance(st, p, f[0], f[1], f[2]);
+        if (d < dmin) dmin = d;
+    }
+    double sigma = scale * dmin;
+    double floor_s = 1.0 / (double)st->S;
+    if (!(sigma >= floor_s)) sigma = floor_s;          /* also when no plane is finite */
+    return sigma;
+}
+
+static int tet_folded(const orc_state *st, const float *X, int t)
+{
+    orc_i3 c[4];
+    for (int i = 0; i < 4; ++i) c[i] = vertex_at(st, X, st->tets[4 * t + i]);
+    return orient_arr(c) <= 0;
+}
+
+/* Repair of one solution in place.  noise: [max_points][64][3] standard
+ * normal draws.  Returns the number of moved points; *sev_raw = sum of
+ * |orient| over the folded copies of both meshes afterwards. */
+int orc_repair(const orc_state *st, float *src, float *tgt, const float *noise, int max_points, double scale,
+               uint64_t *sev_raw)
+{
+    const orc_problem *P = &st->p;
+    int moved = 0, visits = 0, stop = 0;
+    char *done = (char *)malloc((size_t)P->n_points);
+    if (!done) return -1;
+    for (int m = 0; m < 2 && !stop; ++m) {
+        float *X = m == 0 ? src : tgt;
+        memset(done, 0, (size_t)P->n_points);
+        for (int t = 0; t < P->n_tets && !stop; ++t) {
+            if (!tet_folded(st, X, t)) continue;
+            for (int i = 0; i < 4 && !stop; ++i) {
+                int v = st->tets[4 * t + i];
+                if (done[v]) continue;
+                done[v] = 1;
+                if (visits >= max_points) { stop = 1; break; }
+                double sigma = repair_sigma(st, X, v, scale);
+                uint64_t before = star_severity(st, X, v, vertex_at(st, X, v));
+                int64_t best_gain = 0;
+                int best_k = -1;
+                float best[3] = {0, 0, 0};
+                for (int k = 0; k < 64; ++k) {
+                    const float *z = noise + ((size_t)visits * 64 + k) * 3;
+                    float q[3];
+                    for (int a = 0; a < 3; ++a) {
+                        double step = sigma * (double)z[a];
+                        double pos = (double)X[3 * (size_t)v + a] + step;
+                        q[a] = (float)pos;
+                    }
+                    uint64_t after = star_severity(st, X, v, snap3(st, q));
+                    int64_t gain = (int64_t)before - (int64_t)after;
+                    if (gain > best_gain) {
+                        best_gain = gain;
+                        best_k = k;
+                        best[0] = q[0]; best[1] = q[1]; best[2] = q[2];
+                    }
+                }
+                ++visits;
+                if (best_k < 0) { stop = 1; break; }          /* every trial deteriorates: abort */
+                for (int a = 0; a < 3; ++a) X[3 * (size_t)v + a] = best[a];
+                ++moved;
+            }
+        }
+    }
+    free(done);
+    uint64_t sev = 0;
+    for (int m = 0; m < 2; ++m) {
+        const float *X = m == 0 ? src : tgt;
+        for (int t = 0; t < P->n_tets; ++t) {
+            orc_i3 c[4];
+            for (int i = 0; i < 4; ++i) c[i] = vertex_at(st, X, st->tets[4 * t + i]);
+            int64_t D = orient_arr(c);
+            if (D <= 0) sev += (uint64_t)(D < 0 ? -D : D);
+        }
+    }
+    *sev_raw = sev;
+    return moved;
+}
+
+double orc_repair_sigma(const orc_state *st, const float *X, int v, double scale)
+{
+    return repair_sigma(st, X, v, scale);
+}
