@@ -309,6 +309,26 @@ morea_status morea_mlp_destroy(morea_mlp *n);
  * b1 [h1], W2 [h2][h1], b2 [h2], W3 [n_out][h2], b3 [n_out]. */
 morea_status morea_mlp_info(const morea_mlp *n, int64_t *n_params, int32_t *padded_inputs);
 
+/* Repair of folded solutions (Sec. 4.3.1), in place, on the stream.
+ *
+ * src, tgt: device [n_sol][V][3] FP32 coordinates of the two meshes of each
+ * solution; updated in place.  noise: device [n_sol][max_points][64][3]
+ * standard normal draws (the caller's random numbers).  For each solution:
+ * the source mesh, then the target mesh; tets in order and, while a tet is
+ * folded, its four vertices in order, each vertex at most once per mesh, at
+ * most max_points visits in all.  A visited vertex gets 64 trial positions
+ * x + sigma z (rounded to FP32) with sigma = scale times its smallest
+ * distance to the plane of a face opposite it in its star (at least
+ * 2^-k voxel); the trial with the largest decrease of the star's fold
+ * severity is kept (lowest index on ties), and the first vertex without a
+ * decreasing trial ends that solution's repair.  moved: device [n_sol]
+ * number of vertices moved; severity: device [n_sol] fold severity of both
+ * meshes afterwards (as morea_check_folds).  The problem's slots and caches
+ * are not touched: evaluate the repaired solutions afterwards.
+ * MOREA_EINVAL: null pointers, n_sol < 1, max_points < 1, scale not > 0. */
+morea_status morea_repair_folds(morea_problem *p, int32_t n_sol, float *src, float *tgt, const float *noise,
+                                int32_t max_points, float scale, int32_t *moved, double *severity, void *stream);
+
 /* Read and clear the network's device status word (synchronises the
  * stream).  Bit 0 (MOREA_DEV_MLP_WAIT_TIMEOUT): a wait inside a
  * tensor-core product gave up (its outputs are invalid).  No counterpart in

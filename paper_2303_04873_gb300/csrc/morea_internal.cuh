@@ -161,6 +161,10 @@ cudaError_t launch_band_dilate(const DevProblem &hp, const uint8_t *band, uint8_
 cudaError_t launch_sample(const DevProblem *probs, const DevProblem &hp, const WorkEntry *entries,
                           const RasterSetup *setup, RasterOut *rout, const int *n_entries_dev, int n_entries_host,
                           int grid, int chunk, int *queue, cudaStream_t st);
+// Repair of folded solutions (k_repair.cu), one warp per solution.
+cudaError_t launch_repair(const DevProblem *dp, const DevProblem &hp, const int *v2t_off, const int *v2t_idx,
+                          int n_sol, float *src, float *tgt, const float *noise, int max_points, double scale,
+                          int *moved, double *severity, cudaStream_t st);
 cudaError_t launch_raster(const DevProblem *probs, const DevProblem &hp, const WorkEntry *entries,
                           const RasterSetup *setup, RasterOut *rout, int2 *bandrows, const int *n_entries_dev,
                           int n_entries_host, int grid, int chunk, int *queue, cudaStream_t st);

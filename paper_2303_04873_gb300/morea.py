@@ -37,7 +37,7 @@ ENTRY_POINTS = (
     "morea_commit_partial", "morea_check_folds", "morea_read_records", "morea_read_totals",
     "morea_partial_features", "morea_mlp_create", "morea_mlp_destroy", "morea_mlp_info",
     "morea_mlp_set_params", "morea_mlp_get_params", "morea_mlp_forward", "morea_mlp_gradients",
-    "morea_mlp_train_step", "morea_mlp_device_status",
+    "morea_mlp_train_step", "morea_mlp_device_status", "morea_repair_folds",
     "morea_device_status", "morea_problem_info", "morea_batch_create", "morea_batch_destroy",
     "morea_batch_eval_full", "morea_batch_capture", "morea_batch_replay", "morea_set_launch",
     "morea_batch_set_launch", "morea_profile", "morea_profile_read", "morea_fold_magnitude_noalloc",
@@ -95,6 +95,7 @@ def lib():
     L.morea_eval_partial.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, u8p, vp, u8p, vp]
     L.morea_commit_partial.argtypes = [vp, i32, u8p, vp]
     L.morea_check_folds.argtypes = [vp, i32, vp, vp, u8p, vp, vp]
+    L.morea_repair_folds.argtypes = [vp, i32, vp, vp, vp, i32, ctypes.c_float, vp, vp, vp]
     L.morea_read_records.argtypes = [vp, i32, vp, vp, vp]
     L.morea_read_totals.argtypes = [vp, i32, vp, vp, vp]
     L.morea_device_status.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_uint32)]
@@ -304,6 +305,21 @@ class Problem:
         n = int(accept.shape[0])
         _check(self._L.morea_commit_partial(self._h, n, _dev(accept, torch.uint8, (n,), "accept"),
                                             _stream(stream)), "morea_commit_partial")
+
+    def repair_folds(self, src: torch.Tensor, tgt: torch.Tensor, noise: torch.Tensor, max_points: int,
+                     scale: float = 1.0, stream=None):
+        """Repair (Sec. 4.3.1) of src/tgt [n][V][3] in place; noise [n][max_points][64][3] N(0,1).
+        Returns (moved [n] int32, severity [n] f64) on the device."""
+        n = int(src.shape[0])
+        V = self.n_points
+        moved = torch.empty((n,), dtype=torch.int32, device=src.device)
+        sev = torch.empty((n,), dtype=torch.float64, device=src.device)
+        _check(self._L.morea_repair_folds(
+            self._h, n, _dev(src, torch.float32, (n, V, 3), "src"), _dev(tgt, torch.float32, (n, V, 3), "tgt"),
+            _dev(noise, torch.float32, (n, int(max_points), 64, 3), "noise"), int(max_points), float(scale),
+            _dev(moved, torch.int32, (n,), "moved"), _dev(sev, torch.float64, (n,), "severity"),
+            _stream(stream)), "morea_repair_folds")
+        return moved, sev
 
     def check_folds(self, src: torch.Tensor, tgt: torch.Tensor, stream=None):
         n = int(src.shape[0])
