@@ -56,10 +56,11 @@ def parse():
     ap.add_argument("--seeds", type=int, default=5, help="c3: EA seeds compared (200, 201, ...)")
     ap.add_argument("--estimator", choices=["voxels", "sampled"], default="voxels",
                     help="c1/c2: voxel centres (default) or the sampled estimator of App. A.2 (1 point per voxel^3)")
-    ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4", "repair"], default="c1",
+    ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4", "repair", "surrogate_train"], default="c1",
                     help="c1: 128x128x96 f32 (the headline); c2: 256x256x160 f16 graded mesh; "
                          "c4: 16 uneven f16 problems in one batched graph launch; "
-                         "repair: fold repair of 128 perturbed solutions")
+                         "repair: fold repair of 128 perturbed solutions; "
+                         "surrogate_train: training steps of the surrogate network")
     return ap.parse_args()
 
 
@@ -650,7 +651,7 @@ def run_surrogate_ea(args):
 
 def run_repair(args):
     """Repair of folded solutions (Sec. 4.3.1) on the 128x128x96 problem: 128
-    solutions whose points are perturbed by N(0, 6^2) voxels on both meshes,
+    solutions whose points are perturbed by N(0, 2.5^2) voxels on both meshes,
     so most of them fold; each step restores the folded coordinates (a
     device copy) and repairs them with 64 trials per visited point and at
     most 64 visits per solution.  value = repaired solutions per second."""
@@ -664,8 +665,8 @@ def run_repair(args):
     p = synth.make_c1()
     n, mp = p.n_solutions, 64
     rng = np.random.default_rng(21)
-    src0 = torch.as_tensor((p.sol_src + rng.normal(0, 6.0, p.sol_src.shape)).astype(np.float32)).to(dev)
-    tgt0 = torch.as_tensor((p.sol_tgt + rng.normal(0, 6.0, p.sol_tgt.shape)).astype(np.float32)).to(dev)
+    src0 = torch.as_tensor((p.sol_src + rng.normal(0, 2.5, p.sol_src.shape)).astype(np.float32)).to(dev)
+    tgt0 = torch.as_tensor((p.sol_tgt + rng.normal(0, 2.5, p.sol_tgt.shape)).astype(np.float32)).to(dev)
     noise = torch.as_tensor(rng.normal(size=(n, mp, 64, 3)).astype(np.float32)).to(dev)
     gp = morea.Problem(p, max_solutions=n)
     folded0, sev0 = gp.check_folds(src0, tgt0)
@@ -694,7 +695,7 @@ def run_repair(args):
         "metric": "repaired solutions/sec", "value": n * args.steps / (total / 1e3), "unit": "solutions/s",
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps,
         "higher_is_better": True, "data": "synthetic", "dtype": "int64/f64 (exact orientations)",
-        "config": {"workload": "repair: 128x128x96, 2304 tets, 128 solutions perturbed N(0, 6^2) voxels, "
+        "config": {"workload": "repair: 128x128x96, 2304 tets, 128 solutions perturbed N(0, 2.5^2) voxels, "
                                "64 trials per visit, at most 64 visits per solution"},
         "folded_before": int(folded0.sum().item()), "folded_after": int(folded1.sum().item()),
         "severity_before_mean": float(sev0.mean().item()), "severity_after_mean": float(sev.mean().item()),
@@ -706,8 +707,65 @@ def run_repair(args):
     return 0
 
 
+def bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops"]), "measured burst cuBLAS bf16"
+    except Exception:
+        return 1900.0, "fallback"
+
+
+def run_surrogate_train(args):
+    """Training of the surrogate network 4563 -> 512 -> 256 -> 3 on batches of
+    1024 random inputs (Adam, BF16 products on tcgen05, FP32 accumulation);
+    value = training samples per second.  The roofline reports the five
+    tensor-core products of a step against the measured BF16 peak."""
+    import torch
+    from paper_2303_04873_gb300 import build as _b
+    _b.build()
+    from paper_2303_04873_gb300 import morea
+    torch.cuda.set_device(0)
+    n_in, h1, h2, n_out, B = 4563, 512, 256, 3, 1024
+    net = morea.Mlp(n_in, h1, h2, n_out, max_batch=B, seed=0)
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.randn(B, n_in, device="cuda", generator=gen)
+    t = torch.randn(B, n_out, device="cuda", generator=gen)
+    kin = net.kin
+    flops = 2 * B * (kin * h1 + h1 * h2) + 2 * B * (h2 * h1 + h1 * h2 + h1 * kin)
+    for _ in range(max(3, args.warmup)):
+        net.train_step(x, t, 1e-4)
+    torch.cuda.synchronize()
+    reps = max(args.steps, 50)
+    clocks = ClockSampler(0)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        net.train_step(x, t, 1e-4)
+    b.record()
+    b.synchronize()
+    ck = clocks.stop()
+    ms = a.elapsed_time(b) / reps
+    peak, kind = bf16_peak()
+    achieved = flops / (ms * 1e-3) / 1e12
+    line = {
+        "metric": "surrogate training samples/sec", "value": B / (ms * 1e-3), "unit": "samples/s",
+        "n_gpus": 1, "steps": reps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "data": "synthetic", "dtype": "bf16 (products) / f32 (accumulation, Adam)",
+        "config": {"workload": "surrogate training: 4563 -> 512 -> 256 -> 3, batch 1024, Adam"},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None, "peak_kind": kind,
+                     "kernel": "the five k_gemm_tc products of a step, timed with the whole step"},
+        "status": net.device_status(), "clocks": ck,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.workload == "surrogate_train" and args.impl != "reference":
+        return run_surrogate_train(args)
     if args.workload == "repair" and args.impl != "reference":
         return run_repair(args)
     if args.impl == "reference":

@@ -3,7 +3,7 @@
 // K-contiguous, FP32 accumulation in tensor memory.
 //
 // One CTA computes one 128 x 128 tile of C with three roles:
-//   warp 0 (one lane)  TMA producer: 128 x 64 tiles of A and B into a 4-stage
+//   warp 0 (one lane)  TMA producer: 128 x 64 tiles of A and B into a 6-stage
 //                      shared-memory ring (128-byte swizzle), completion on
 //                      the stage's "full" mbarrier;
 //   warp 1             allocates 128 TMEM columns; one lane issues four
@@ -34,7 +34,7 @@ namespace {
 
 using bf16 = __nv_bfloat16;
 
-constexpr int TBM = 128, TBN = 128, TBK = 64, TST = 4;
+constexpr int TBM = 128, TBN = 128, TBK = 64, TST = 6;
 constexpr int kTileA = TBM * TBK * 2;                  // 16 KB
 constexpr int kTileB = TBN * TBK * 2;                  // 16 KB
 constexpr int kStage = kTileA + kTileB;
@@ -349,8 +349,10 @@ int mlp_gemm_splits(int M, int N, int K)
 {
     const long long tiles = (long long)((M + TBM - 1) / TBM) * ((N + TBN - 1) / TBN);
     const int nk = (K + TBK - 1) / TBK;
-    // enough CTAs to cover the SMs, at least 8 k-blocks each, at most 8 splits
-    long long s = std::min<long long>(nk / 8, (148 + tiles - 1) / tiles);
+    // enough CTAs to cover the SMs, at least 2 k-blocks each, at most 8 splits
+    // (one CTA streams its operands through TMA at a bounded rate, so short
+    // products gain from more CTAs even at the cost of the ordered reduction)
+    long long s = std::min<long long>(nk / 2, (148 + tiles - 1) / tiles);
     return (int)std::max<long long>(1, std::min<long long>(s, 8));
 }
 
