@@ -125,6 +125,9 @@ def lib():
         L.orc_repair.restype = ctypes.c_int
         L.orc_repair_sigma.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double]
         L.orc_repair_sigma.restype = ctypes.c_double
+        L.orc_dvf.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+        L.orc_dvf.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -257,6 +260,24 @@ class Oracle:
             raise OracleError("oracle repair failed")
         S = float(1 << int(self._P.subvoxel_bits))
         return s, t, int(moved), sev.value / (6.0 * S * S * S)
+
+    def dvf(self, src, tgt, side: int, labels_own=None, labels_other=None, n_labels: int = 0):
+        """R15: displacement field [nz][ny][nx][3] (NaN outside) and, with
+        labels, the per-label counts [n_labels][3] (own, pulled back, both)."""
+        s = np.ascontiguousarray(src, dtype=np.float32)
+        t = np.ascontiguousarray(tgt, dtype=np.float32)
+        out = np.zeros((self.nz, self.ny, self.nx, 3), np.float64)
+        counts = None
+        lo = lt = None
+        if labels_own is not None:
+            lo = np.ascontiguousarray(labels_own, dtype=np.uint8)
+            lt = np.ascontiguousarray(labels_other, dtype=np.uint8)
+            counts = np.zeros((n_labels, 3), np.int64)
+        rc = self._L.orc_dvf(self._h, _ptr(s), _ptr(t), int(side), _ptr(out), _ptr(lo), _ptr(lt), int(n_labels),
+                             _ptr(counts))
+        if rc != 0:
+            raise OracleError("oracle dvf failed")
+        return out, counts
 
     def repair_sigma(self, X, v: int, scale: float = 1.0) -> float:
         x = np.ascontiguousarray(X, dtype=np.float32)

@@ -83,6 +83,16 @@
  *      decreases it, the repair of the solution stops.  At most max_points
  *      visits per solution.  FP64 without contraction, so the float trial
  *      positions are the same on every machine.
+ *   R15 displacement field and label overlap (the evaluation of Sec. 5):
+ *      for every voxel centre p of one image inside an unfolded copy (R3),
+ *      dvf(p) = T(p) - p with the FP64 barycentric map; voxels in no copy
+ *      are NaN, and a voxel inside several copies (folded or overlapping
+ *      meshes only) takes the first copy in tet order.  Label overlap: the
+ *      nearest voxel of the other image to T(p) (round half to even,
+ *      clamped to the image) gives the pulled-back label, with T(p) taken
+ *      in the GPU kernel's FP32 arithmetic because floating point decides
+ *      the integer (as R9); per label l the counts of covered voxels with
+ *      own label l, with pulled-back label l, and with both.
  */
 #include <math.h>
 #include <stdint.h>
@@ -254,10 +264,12 @@ static double h_fn(int mode, double a, double b)
 
 /* R9: the FP32 sample of the other image at the image of voxel (i, j, k),
  * used only to decide the case of h in mode 1. */
-static float sample_fp32_case(const orc_state *st, const orc_i3 own[4], const orc_i3 oth[4], int64_t D,
-                              const double *img, int64_t i, int64_t j, int64_t k)
+/* The affine map of the GPU kernel in its FP32 arithmetic (R9, R15):
+ * M = F adj(E) / D rounded to float, then y = t0 + M (p - s0) with fused
+ * multiply-adds in the kernel's order, for the voxel centre (i, j, k). */
+static void map_fp32(const orc_state *st, const orc_i3 own[4], const orc_i3 oth[4], int64_t D, int64_t i,
+                     int64_t j, int64_t k, float y[3])
 {
-    const orc_problem *P = &st->p;
     int64_t e[3][3], f[3][3];
     for (int m = 0; m < 3; ++m) {
         e[m][0] = own[m + 1].x - own[0].x; e[m][1] = own[m + 1].y - own[0].y; e[m][2] = own[m + 1].z - own[0].z;
@@ -281,12 +293,20 @@ static float sample_fp32_case(const orc_state *st, const orc_i3 own[4], const or
     const float t0[3] = {(float)oth[0].x * inv_s - 0.5f, (float)oth[0].y * inv_s - 0.5f,
                          (float)oth[0].z * inv_s - 0.5f};
     const float d[3] = {(float)i - s0[0], (float)j - s0[1], (float)k - s0[2]};
+    for (int a = 0; a < 3; ++a) y[a] = fmaf(M[a][0], d[0], fmaf(M[a][1], d[1], fmaf(M[a][2], d[2], t0[a])));
+}
+
+static float sample_fp32_case(const orc_state *st, const orc_i3 own[4], const orc_i3 oth[4], int64_t D,
+                              const double *img, int64_t i, int64_t j, int64_t k)
+{
+    const orc_problem *P = &st->p;
+    float y[3];
+    map_fp32(st, own, oth, D, i, j, k, y);
     const int n[3] = {P->nx, P->ny, P->nz};
     float c[3], fr[3];
     int i0[3];
     for (int a = 0; a < 3; ++a) {
-        float y = fmaf(M[a][0], d[0], fmaf(M[a][1], d[1], fmaf(M[a][2], d[2], t0[a])));
-        c[a] = fminf(fmaxf(y, 0.0f), (float)(n[a] - 1));
+        c[a] = fminf(fmaxf(y[a], 0.0f), (float)(n[a] - 1));
         i0[a] = (int)c[a];
         if (i0[a] > n[a] - 2) i0[a] = n[a] - 2;
         fr[a] = c[a] - (float)i0[a];
@@ -952,4 +972,80 @@ int orc_repair(const orc_state *st, float *src, float *tgt, const float *noise, 
 double orc_repair_sigma(const orc_state *st, const float *X, int v, double scale)
 {
     return repair_sigma(st, X, v, scale);
+}
+
+/* ------------------------------------------------------------------ */
+/* R15: displacement field and label overlap                           */
+/* ------------------------------------------------------------------ */
+
+int orc_dvf(const orc_state *st, const float *src, const float *tgt, int side, double *dvf,
+            const uint8_t *lab_own, const uint8_t *lab_oth, int n_labels, int64_t *counts)
+{
+    const orc_problem *P = &st->p;
+    const size_t N = (size_t)P->nx * P->ny * P->nz;
+    char *covered = (char *)calloc(N, 1);
+    if (!covered) return ORC_ENOMEM;
+    if (dvf)
+        for (size_t q = 0; q < 3 * N; ++q) dvf[q] = NAN;
+    if (counts) memset(counts, 0, sizeof(int64_t) * 3 * (size_t)n_labels);
+    const float *Xo = side == 0 ? src : tgt, *Xt = side == 0 ? tgt : src;
+    int64_t S = st->S, H = st->S / 2;
+    int n[3] = {P->nx, P->ny, P->nz};
+    for (int t = 0; t < P->n_tets; ++t) {
+        orc_i3 own[4], oth[4];
+        for (int i = 0; i < 4; ++i) {
+            int v = st->tets[4 * t + i];
+            own[i] = snap3(st, Xo + 3 * (size_t)v);
+            oth[i] = snap3(st, Xt + 3 * (size_t)v);
+        }
+        int64_t D = orient_arr(own);
+        if (D <= 0) continue;                              /* folded copy: not rasterised */
+        int64_t lo[3], hi[3];
+        for (int a = 0; a < 3; ++a) {
+            int64_t mn = INT64_MAX, mx = INT64_MIN;
+            for (int i = 0; i < 4; ++i) {
+                int64_t c = a == 0 ? own[i].x : a == 1 ? own[i].y : own[i].z;
+                if (c < mn) mn = c;
+                if (c > mx) mx = c;
+            }
+            lo[a] = ceil_div(mn - H, S);
+            hi[a] = floor_div(mx - H, S);
+            if (lo[a] < 0) lo[a] = 0;
+            if (hi[a] > n[a] - 1) hi[a] = n[a] - 1;
+        }
+        for (int64_t k = lo[2]; k <= hi[2]; ++k)
+            for (int64_t j = lo[1]; j <= hi[1]; ++j)
+                for (int64_t i = lo[0]; i <= hi[0]; ++i) {
+                    orc_i3 p = {i * S + H, j * S + H, k * S + H};
+                    if (!inside_sos(own, p)) continue;
+                    size_t idx = ((size_t)k * P->ny + (size_t)j) * P->nx + (size_t)i;
+                    if (covered[idx]) continue;
+                    covered[idx] = 1;
+                    if (dvf) {
+                        double y[3];
+                        bary_map(st, own, D, oth, p, y);
+                        dvf[3 * idx] = y[0] - (double)i;
+                        dvf[3 * idx + 1] = y[1] - (double)j;
+                        dvf[3 * idx + 2] = y[2] - (double)k;
+                    }
+                    if (counts) {
+                        float y32[3];
+                        map_fp32(st, own, oth, D, i, j, k, y32);
+                        int64_t m[3];
+                        for (int a = 0; a < 3; ++a) {
+                            float r = rintf(y32[a]);
+                            if (!(r >= 0.0f)) r = 0.0f;
+                            if (r > (float)(n[a] - 1)) r = (float)(n[a] - 1);
+                            m[a] = (int64_t)r;
+                        }
+                        size_t jdx = ((size_t)m[2] * P->ny + (size_t)m[1]) * P->nx + (size_t)m[0];
+                        int la = lab_own[idx], lb = lab_oth[jdx];
+                        if (la < n_labels) counts[3 * la] += 1;
+                        if (lb < n_labels) counts[3 * lb + 1] += 1;
+                        if (la == lb && la < n_labels) counts[3 * la + 2] += 1;
+                    }
+                }
+    }
+    free(covered);
+    return ORC_OK;
 }
