@@ -329,6 +329,27 @@ morea_status morea_mlp_info(const morea_mlp *n, int64_t *n_params, int32_t *padd
 morea_status morea_repair_folds(morea_problem *p, int32_t n_sol, float *src, float *tgt, const float *noise,
                                 int32_t max_points, float scale, int32_t *moved, double *severity, void *stream);
 
+/* Displacement field of one solution and the label overlap it implies (the
+ * evaluation of Sec. 5; not part of the objectives).
+ *
+ * src, tgt: device [V][3] FP32 coordinates of the solution's two meshes.
+ * side 0: for every voxel centre p of the source image inside an unfolded
+ * source copy (the exact association of morea_eval_full), dvf(p) = T(p) - p
+ * (the forward field); side 1: the same on the target image with T'.
+ * dvf: device [nz][ny][nx][3] FP32, or NULL; voxels in no copy are NaN.
+ * labels_own / labels_other: device [nz][ny][nx] uint8 label images of
+ * this side and of the other side, or both NULL; with them, overlap: device
+ * int64 [n_labels][3] = per label l the number of covered voxels with own
+ * label l, with label l at the voxel of the other image nearest to T(p)
+ * (round half to even, clamped), and with both (Dice = 2 c2 / (c0 + c1)).
+ * n_labels <= 64; labels >= n_labels are not counted.  A voxel inside
+ * several copies (only with folded or overlapping meshes) is written by one
+ * of them and counted once per copy.  MOREA_EINVAL: null p/src/tgt, side
+ * not 0/1, labels without overlap or n_labels out of range. */
+morea_status morea_displacement(morea_problem *p, const float *src, const float *tgt, int32_t side, float *dvf,
+                                const uint8_t *labels_own, const uint8_t *labels_other, int32_t n_labels,
+                                int64_t *overlap, void *stream);
+
 /* Read and clear the network's device status word (synchronises the
  * stream).  Bit 0 (MOREA_DEV_MLP_WAIT_TIMEOUT): a wait inside a
  * tensor-core product gave up (its outputs are invalid).  No counterpart in

@@ -1,7 +1,8 @@
-// Device helpers shared by the image passes (k_raster.cu, k_sample.cu):
-// image and quad loads, trilinear sampling with the clamping of reading R4,
-// h of Sec. 4.1.2, compensated FP32 accumulation and its warp reduction, and
-// the item scheduler.  Internal; each translation unit gets its own copy.
+// Device helpers shared by the image passes (k_raster.cu, k_sample.cu,
+// k_dvf.cu): image and quad loads, trilinear sampling with the clamping of
+// reading R4, h of Sec. 4.1.2, compensated FP32 accumulation and its warp
+// reduction, the item scheduler, and the exact row intervals of a tet copy
+// (reading R3).  Internal; each translation unit gets its own copy.
 #pragma once
 
 #include "morea_device.cuh"
@@ -161,6 +162,112 @@ __device__ __forceinline__ void run_items(int n_items, int chunk, int *queue, F 
         const int end = min(base + chunk, n_items);
         for (int item = base; item < end; ++item) body(item);
     }
+}
+
+// ---- exact voxel association of one tet copy (reading R3) ----
+
+// Smallest i in [ilo, ihi + 1] with A i + B > 0 (A > 0); ihi + 1 if none.
+__device__ __forceinline__ int face_lo(long long A, long long B, float est, int ilo, int ihi)
+{
+    const float ec = fminf(fmaxf(est, (float)(ilo - 1)), (float)(ihi + 1));
+    int i = (int)floorf(ec) + 1;
+    i = min(max(i, ilo), ihi + 1);
+    while (i > ilo && A * (long long)(i - 1) + B > 0) --i;
+    while (i <= ihi && A * (long long)i + B <= 0) ++i;
+    return i;
+}
+
+// Largest i in [ilo - 1, ihi] with A i + B > 0 (A < 0); ilo - 1 if none.
+__device__ __forceinline__ int face_hi(long long A, long long B, float est, int ilo, int ihi)
+{
+    const float ec = fminf(fmaxf(est, (float)(ilo - 1)), (float)(ihi + 1));
+    int i = (int)ceilf(ec) - 1;
+    i = min(max(i, ilo - 1), ihi);
+    while (i < ihi && A * (long long)(i + 1) + B > 0) ++i;
+    while (i >= ilo && A * (long long)i + B <= 0) --i;
+    return i;
+}
+
+// Exact x-interval [lo, hi] of the voxel centres of row (jlo + dj, klo + dk).
+// Per face the FP32 root estimate decides whenever it is farther than the
+// face's error bound from the bounding-box ends and from every integer;
+// otherwise the bound is solved exactly in int64.
+// Loads of a copy's face rows: through the read-only data cache when the
+// rows are in global memory (the image passes), plain loads when a caller
+// keeps them in shared memory (k_dvf); ld.global.nc must never see a shared
+// address.
+template <bool GLOBAL, typename T>
+__device__ __forceinline__ T face_load(const T *p)
+{
+    if (GLOBAL) return __ldg(p);
+    return *p;
+}
+
+template <bool GLOBAL = true>
+__device__ __forceinline__ void row_interval(const FaceRow *__restrict__ f, int dj, int dk, int ilo, int ihi,
+                                             int &lo, int &hi)
+{
+    lo = ilo;
+    hi = ihi;
+    const float fdj = (float)dj, fdk = (float)dk;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float4 es = face_load<GLOBAL>(reinterpret_cast<const float4 *>(&f[q].e0));       // e0, ey, ez, signed tol
+        if (isinf(es.w)) {                    // face parallel to x: the whole row or nothing
+            const longlong2 ab = face_load<GLOBAL>(reinterpret_cast<const longlong2 *>(&f[q].ax));
+            const longlong2 yz = face_load<GLOBAL>(reinterpret_cast<const longlong2 *>(&f[q].by));
+            if (ab.y + yz.x * dj + yz.y * dk <= 0) hi = lo - 1;
+            continue;
+        }
+        const float est = fmaf(es.y, fdj, fmaf(es.z, fdk, es.x));
+        const float tol = fabsf(es.w);
+        const float fl = floorf(est);
+        const float fr = est - fl;
+        if (es.w > 0.0f) {                    // ax > 0, inside for i > root: lo = floor(root) + 1
+            if (est + tol < (float)ilo) continue;
+            if (est - tol >= (float)ihi) { hi = lo - 1; continue; }
+            if (fr > tol && fr < 1.0f - tol) { lo = max(lo, (int)fl + 1); continue; }
+            const longlong2 ab = face_load<GLOBAL>(reinterpret_cast<const longlong2 *>(&f[q].ax));
+            const longlong2 yz = face_load<GLOBAL>(reinterpret_cast<const longlong2 *>(&f[q].by));
+            lo = max(lo, face_lo(ab.x, ab.y + yz.x * dj + yz.y * dk, est, ilo, ihi));
+        } else {                              // ax < 0, inside for i < root: hi = ceil(root) - 1
+            if (est - tol > (float)ihi) continue;
+            if (est + tol <= (float)ilo) { hi = lo - 1; continue; }
+            if (fr > tol && fr < 1.0f - tol) { hi = min(hi, (int)fl); continue; }
+            const longlong2 ab = face_load<GLOBAL>(reinterpret_cast<const longlong2 *>(&f[q].ax));
+            const longlong2 yz = face_load<GLOBAL>(reinterpret_cast<const longlong2 *>(&f[q].by));
+            hi = min(hi, face_hi(ab.x, ab.y + yz.x * dj + yz.y * dk, est, ilo, ihi));
+        }
+    }
+}
+
+// y-extent [y0, y1] (snapped units) of the cross-section of a tet copy with
+// the plane z = zq: the intersections of its six edges with the plane.  The
+// vertices are integers below 2^17, so each intersection is within 2^-6 of
+// its exact value (one rounded division and one FMA); callers widen the
+// extent by more than that.  Empty (y0 > y1) if no edge meets the plane.
+__device__ __forceinline__ void slice_y_extent(const int4 *vq, float zq, float &y0, float &y1)
+{
+    float y[4], z[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const int4 t = __ldg(vq + v);
+        y[v] = (float)t.y;
+        z[v] = (float)t.z;
+    }
+    y0 = INFINITY;
+    y1 = -INFINITY;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = a + 1; b < 4; ++b) {
+            if (fminf(z[a], z[b]) <= zq && zq <= fmaxf(z[a], z[b])) {
+                float ya = y[a], yb = y[b];
+                if (z[a] != z[b]) ya = yb = fmaf((zq - z[a]) / (z[b] - z[a]), y[b] - y[a], y[a]);
+                y0 = fminf(y0, fminf(ya, yb));
+                y1 = fmaxf(y1, fmaxf(ya, yb));
+            }
+        }
 }
 
 }  // namespace

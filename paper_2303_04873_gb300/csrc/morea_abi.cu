@@ -501,6 +501,21 @@ morea_status morea_commit_partial(morea_problem *p, int32_t n_req, const uint8_t
                                            (cudaStream_t)stream));
 }
 
+morea_status morea_displacement(morea_problem *p, const float *src, const float *tgt, int32_t side, float *dvf,
+                                const uint8_t *labels_own, const uint8_t *labels_other, int32_t n_labels,
+                                int64_t *overlap, void *stream)
+{
+    if (!p || !src || !tgt || (side != 0 && side != 1)) return MOREA_EINVAL;
+    const bool labels = labels_own || labels_other || overlap;
+    if (labels && (!labels_own || !labels_other || !overlap || n_labels < 1 || n_labels > dvf_max_labels()))
+        return MOREA_EINVAL;
+    DeviceGuard g(p->device);
+    return from_cuda(launch_dvf(p->dp, p->hp, src, tgt, side, dvf, labels ? labels_own : nullptr,
+                                labels ? labels_other : nullptr, labels ? n_labels : 0,
+                                labels ? reinterpret_cast<unsigned long long *>(overlap) : nullptr,
+                                (cudaStream_t)stream));
+}
+
 morea_status morea_repair_folds(morea_problem *p, int32_t n_sol, float *src, float *tgt, const float *noise,
                                 int32_t max_points, float scale, int32_t *moved, double *severity, void *stream)
 {

@@ -161,6 +161,11 @@ cudaError_t launch_band_dilate(const DevProblem &hp, const uint8_t *band, uint8_
 cudaError_t launch_sample(const DevProblem *probs, const DevProblem &hp, const WorkEntry *entries,
                           const RasterSetup *setup, RasterOut *rout, const int *n_entries_dev, int n_entries_host,
                           int grid, int chunk, int *queue, cudaStream_t st);
+// Displacement field and label overlap of one solution (k_dvf.cu).
+int dvf_max_labels();
+cudaError_t launch_dvf(const DevProblem *dp, const DevProblem &hp, const float *src, const float *tgt, int side,
+                       float *dvf, const uint8_t *lab_own, const uint8_t *lab_oth, int n_labels,
+                       unsigned long long *counts, cudaStream_t st);
 // Repair of folded solutions (k_repair.cu), one warp per solution.
 cudaError_t launch_repair(const DevProblem *dp, const DevProblem &hp, const int *v2t_off, const int *v2t_idx,
                           int n_sol, float *src, float *tgt, const float *noise, int max_points, double scale,

@@ -37,7 +37,7 @@ ENTRY_POINTS = (
     "morea_commit_partial", "morea_check_folds", "morea_read_records", "morea_read_totals",
     "morea_partial_features", "morea_mlp_create", "morea_mlp_destroy", "morea_mlp_info",
     "morea_mlp_set_params", "morea_mlp_get_params", "morea_mlp_forward", "morea_mlp_gradients",
-    "morea_mlp_train_step", "morea_mlp_device_status", "morea_repair_folds",
+    "morea_mlp_train_step", "morea_mlp_device_status", "morea_repair_folds", "morea_displacement",
     "morea_device_status", "morea_problem_info", "morea_batch_create", "morea_batch_destroy",
     "morea_batch_eval_full", "morea_batch_capture", "morea_batch_replay", "morea_set_launch",
     "morea_batch_set_launch", "morea_profile", "morea_profile_read", "morea_fold_magnitude_noalloc",
@@ -96,6 +96,7 @@ def lib():
     L.morea_commit_partial.argtypes = [vp, i32, u8p, vp]
     L.morea_check_folds.argtypes = [vp, i32, vp, vp, u8p, vp, vp]
     L.morea_repair_folds.argtypes = [vp, i32, vp, vp, vp, i32, ctypes.c_float, vp, vp, vp]
+    L.morea_displacement.argtypes = [vp, vp, vp, i32, vp, vp, vp, i32, vp, vp]
     L.morea_read_records.argtypes = [vp, i32, vp, vp, vp]
     L.morea_read_totals.argtypes = [vp, i32, vp, vp, vp]
     L.morea_device_status.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_uint32)]
@@ -320,6 +321,27 @@ class Problem:
             _dev(moved, torch.int32, (n,), "moved"), _dev(sev, torch.float64, (n,), "severity"),
             _stream(stream)), "morea_repair_folds")
         return moved, sev
+
+    def displacement(self, src: torch.Tensor, tgt: torch.Tensor, side: int = 0, labels_own=None,
+                     labels_other=None, n_labels: int = 0, stream=None):
+        """Displacement field [nz][ny][nx][3] of one solution (src, tgt [V][3]) on
+        image ``side`` (NaN outside the mesh) and, with label images, the per-label
+        counts [n_labels][3] (own, pulled back, both).  Device tensors."""
+        V = self.n_points
+        dev = src.device
+        dvf = torch.empty((self.nz, self.ny, self.nx, 3), dtype=torch.float32, device=dev)
+        counts = None
+        lo = lt = None
+        if labels_own is not None:
+            counts = torch.empty((int(n_labels), 3), dtype=torch.int64, device=dev)
+            lo = _dev(labels_own, torch.uint8, (self.nz, self.ny, self.nx), "labels_own")
+            lt = _dev(labels_other, torch.uint8, (self.nz, self.ny, self.nx), "labels_other")
+        _check(self._L.morea_displacement(
+            self._h, _dev(src, torch.float32, (V, 3), "src"), _dev(tgt, torch.float32, (V, 3), "tgt"), int(side),
+            _dev(dvf, torch.float32, None, "dvf"), lo, lt, int(n_labels),
+            None if counts is None else _dev(counts, torch.int64, None, "overlap"), _stream(stream)),
+            "morea_displacement")
+        return dvf, counts
 
     def check_folds(self, src: torch.Tensor, tgt: torch.Tensor, stream=None):
         n = int(src.shape[0])
