@@ -329,6 +329,22 @@ morea_status morea_mlp_info(const morea_mlp *n, int64_t *n_params, int32_t *padd
 morea_status morea_repair_folds(morea_problem *p, int32_t n_sol, float *src, float *tgt, const float *noise,
                                 int32_t max_points, float scale, int32_t *moved, double *severity, void *stream);
 
+/* Linkage model and parallel groups of the partial evaluations (Sec. 4.2.1).
+ * Host call; needs no GPU.  tets: host [n_tets][4] topology.  The FOS
+ * elements are mesh edges chosen by a greedy set cover of the points (the
+ * first edge in sorted (a < b) order among those covering the most
+ * uncovered points); two elements interact when the tets containing their
+ * points overlap; DSATUR colours the interaction graph (most distinct
+ * neighbour colours, then largest degree, then lowest index; smallest free
+ * colour).  Outputs (host): elements [n_elements][2] point pairs in the
+ * order the cover takes them, group [n_elements] colours in
+ * [0, n_groups).  Elements of one group touch disjoint tets, so one
+ * morea_eval_partial call may carry a request for each of them on the same
+ * slot.  MOREA_EINVAL: bad sizes or ids, a point in no tet, or more than
+ * max_elements elements. */
+morea_status morea_parallel_groups(int32_t n_points, int32_t n_tets, const int32_t *tets, int32_t max_elements,
+                                   int32_t *elements, int32_t *group, int32_t *n_elements, int32_t *n_groups);
+
 /* Displacement field of one solution and the label overlap it implies (the
  * evaluation of Sec. 5; not part of the objectives).
  *

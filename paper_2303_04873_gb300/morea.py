@@ -38,6 +38,7 @@ ENTRY_POINTS = (
     "morea_partial_features", "morea_mlp_create", "morea_mlp_destroy", "morea_mlp_info",
     "morea_mlp_set_params", "morea_mlp_get_params", "morea_mlp_forward", "morea_mlp_gradients",
     "morea_mlp_train_step", "morea_mlp_device_status", "morea_repair_folds", "morea_displacement",
+    "morea_parallel_groups",
     "morea_device_status", "morea_problem_info", "morea_batch_create", "morea_batch_destroy",
     "morea_batch_eval_full", "morea_batch_capture", "morea_batch_replay", "morea_set_launch",
     "morea_batch_set_launch", "morea_profile", "morea_profile_read", "morea_fold_magnitude_noalloc",
@@ -97,6 +98,7 @@ def lib():
     L.morea_check_folds.argtypes = [vp, i32, vp, vp, u8p, vp, vp]
     L.morea_repair_folds.argtypes = [vp, i32, vp, vp, vp, i32, ctypes.c_float, vp, vp, vp]
     L.morea_displacement.argtypes = [vp, vp, vp, i32, vp, vp, vp, i32, vp, vp]
+    L.morea_parallel_groups.argtypes = [i32, i32, vp, i32, vp, vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
     L.morea_read_records.argtypes = [vp, i32, vp, vp, vp]
     L.morea_read_totals.argtypes = [vp, i32, vp, vp, vp]
     L.morea_device_status.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_uint32)]
@@ -132,6 +134,19 @@ def lib():
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
+
+
+def parallel_groups(n_points: int, tets):
+    """Edge FOS elements [m][2] and their parallel group ids [m] (Sec. 4.2.1; host call)."""
+    t = np.ascontiguousarray(tets, dtype=np.int32)
+    cap = max(1, int(n_points))
+    el = np.zeros((cap, 2), np.int32)
+    grp = np.zeros(cap, np.int32)
+    m, g = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().morea_parallel_groups(int(n_points), int(t.shape[0]), t.ctypes.data_as(ctypes.c_void_p), cap,
+                                       el.ctypes.data_as(ctypes.c_void_p), grp.ctypes.data_as(ctypes.c_void_p),
+                                       ctypes.byref(m), ctypes.byref(g)), "morea_parallel_groups")
+    return el[:m.value].copy(), grp[:m.value].copy()
 
 
 def status_string(code: int) -> str:
