@@ -120,7 +120,7 @@ struct RowQueue {
 
 // Image pass (a4, a5, a7): one warp per (entry, side).
 template <typename TI, int HMODE, int PASS>
-__global__ void __launch_bounds__(kBlock, 4) k_raster(const DevProblem *__restrict__ probs,
+__global__ void __launch_bounds__(kBlock, 6) k_raster(const DevProblem *__restrict__ probs,
                                                      const WorkEntry *__restrict__ entries,
                                                      const RasterSetup *__restrict__ setup,
                                                      RasterOut *__restrict__ rout, int2 *__restrict__ bandrows,
