@@ -49,8 +49,8 @@ def _store(path: str, table: Dict[str, list]):
 def signature(problems: Sequence, n_sol: Sequence[int], kind: str) -> str:
     """Cache key: GPU name, kind of call and the shape of every problem."""
     dev = torch.cuda.get_device_name(torch.cuda.current_device())
-    parts = [f"{p.nx}x{p.ny}x{p.nz}:{p.n_tets}:d{p.dtype}:h{p.h_mode}:g{p.g_mode}:n{n}"
-             for p, n in zip(problems, n_sol)]
+    parts = [f"{p.nx}x{p.ny}x{p.nz}:{p.n_tets}:d{p.dtype}:h{p.h_mode}:g{p.g_mode}"
+             f":e{getattr(p, 'estimator', 0)}:n{n}" for p, n in zip(problems, n_sol)]
     return f"{dev}|{kind}|" + ";".join(parts)
 
 
