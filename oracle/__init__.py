@@ -126,7 +126,7 @@ def lib():
         L.orc_repair_sigma.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double]
         L.orc_repair_sigma.restype = ctypes.c_double
         L.orc_dvf.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
-                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
         L.orc_dvf.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -274,10 +274,23 @@ class Oracle:
             lt = np.ascontiguousarray(labels_other, dtype=np.uint8)
             counts = np.zeros((n_labels, 3), np.int64)
         rc = self._L.orc_dvf(self._h, _ptr(s), _ptr(t), int(side), _ptr(out), _ptr(lo), _ptr(lt), int(n_labels),
-                             _ptr(counts))
+                             _ptr(counts), None)
         if rc != 0:
             raise OracleError("oracle dvf failed")
         return out, counts
+
+    def warp_labels(self, src, tgt, side: int, labels_other):
+        """R15/R17: the other image's label at the voxel nearest to T(p) for
+        every voxel centre p covered by an unfolded copy of mesh ``side``;
+        255 where no copy covers p."""
+        s = np.ascontiguousarray(src, dtype=np.float32)
+        t = np.ascontiguousarray(tgt, dtype=np.float32)
+        lt = np.ascontiguousarray(labels_other, dtype=np.uint8)
+        warped = np.zeros((self.nz, self.ny, self.nx), np.uint8)
+        rc = self._L.orc_dvf(self._h, _ptr(s), _ptr(t), int(side), None, None, _ptr(lt), 0, None, _ptr(warped))
+        if rc != 0:
+            raise OracleError("oracle warp_labels failed")
+        return warped
 
     def repair_sigma(self, X, v: int, scale: float = 1.0) -> float:
         x = np.ascontiguousarray(X, dtype=np.float32)

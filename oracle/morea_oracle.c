@@ -92,7 +92,8 @@
  *      clamped to the image) gives the pulled-back label, with T(p) taken
  *      in the GPU kernel's FP32 arithmetic because floating point decides
  *      the integer (as R9); per label l the counts of covered voxels with
- *      own label l, with pulled-back label l, and with both.
+ *      own label l, with pulled-back label l, and with both.  The warped
+ *      label image holds the pulled-back label per voxel, 255 in no copy.
  */
 #include <math.h>
 #include <stdint.h>
@@ -979,7 +980,7 @@ double orc_repair_sigma(const orc_state *st, const float *X, int v, double scale
 /* ------------------------------------------------------------------ */
 
 int orc_dvf(const orc_state *st, const float *src, const float *tgt, int side, double *dvf,
-            const uint8_t *lab_own, const uint8_t *lab_oth, int n_labels, int64_t *counts)
+            const uint8_t *lab_own, const uint8_t *lab_oth, int n_labels, int64_t *counts, uint8_t *warped)
 {
     const orc_problem *P = &st->p;
     const size_t N = (size_t)P->nx * P->ny * P->nz;
@@ -988,6 +989,7 @@ int orc_dvf(const orc_state *st, const float *src, const float *tgt, int side, d
     if (dvf)
         for (size_t q = 0; q < 3 * N; ++q) dvf[q] = NAN;
     if (counts) memset(counts, 0, sizeof(int64_t) * 3 * (size_t)n_labels);
+    if (warped) memset(warped, 255, N);                   /* 255: in no copy */
     const float *Xo = side == 0 ? src : tgt, *Xt = side == 0 ? tgt : src;
     int64_t S = st->S, H = st->S / 2;
     int n[3] = {P->nx, P->ny, P->nz};
@@ -1028,7 +1030,7 @@ int orc_dvf(const orc_state *st, const float *src, const float *tgt, int side, d
                         dvf[3 * idx + 1] = y[1] - (double)j;
                         dvf[3 * idx + 2] = y[2] - (double)k;
                     }
-                    if (counts) {
+                    if (counts || warped) {
                         float y32[3];
                         map_fp32(st, own, oth, D, i, j, k, y32);
                         int64_t m[3];
@@ -1039,7 +1041,10 @@ int orc_dvf(const orc_state *st, const float *src, const float *tgt, int side, d
                             m[a] = (int64_t)r;
                         }
                         size_t jdx = ((size_t)m[2] * P->ny + (size_t)m[1]) * P->nx + (size_t)m[0];
-                        int la = lab_own[idx], lb = lab_oth[jdx];
+                        int lb = lab_oth[jdx];
+                        if (warped) warped[idx] = (uint8_t)lb;
+                        if (!counts) continue;
+                        int la = lab_own[idx];
                         if (la < n_labels) counts[3 * la] += 1;
                         if (lb < n_labels) counts[3 * lb + 1] += 1;
                         if (la == lb && la < n_labels) counts[3 * la + 2] += 1;

@@ -14,6 +14,7 @@ from .phantom import (  # noqa: F401
     make_c2,
     make_c4,
     kuhn_lattice,
+    label_pair,
     lattice_points,
     jitter_population,
     partial_requests,

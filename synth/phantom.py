@@ -114,6 +114,21 @@ def phantom_pair(shape_xyz, ellipsoids, background, amp, noise_sigma,
     return img_s.astype(np_dtype), img_t.astype(np_dtype)
 
 
+def label_pair(shape_xyz, ellipsoids, amp):
+    """Organ masks of a phantom pair: uint8 label images [nz][ny][nx] of the
+    source and of the target (warped by the same displacement as the images),
+    0 for background and i + 1 inside ellipsoid i (the last one wins)."""
+    nx, ny, nz = shape_xyz
+    z, y, x = np.meshgrid(np.arange(nz, dtype=np.float64),
+                          np.arange(ny, dtype=np.float64),
+                          np.arange(nx, dtype=np.float64), indexing="ij")
+    ids = [e[:6] + (float(i + 1),) for i, e in enumerate(ellipsoids)]
+    lab_s = _paint(x, y, z, 0.0, ids)
+    ux, uy, uz = _displacement(x, y, z, shape_xyz, amp)
+    lab_t = _paint(x + ux, y + uy, z + uz, 0.0, ids)
+    return lab_s.astype(np.uint8), lab_t.astype(np.uint8)
+
+
 # ---------------------------------------------------------------------------
 # meshes
 # ---------------------------------------------------------------------------
