@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--seeds", type=int, default=5, help="c3: EA seeds compared (200, 201, ...)")
     ap.add_argument("--estimator", choices=["voxels", "sampled"], default="voxels",
                     help="c1/c2: voxel centres (default) or the sampled estimator of App. A.2 (1 point per voxel^3)")
-    ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4", "repair", "surrogate_train", "groups"],
+    ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4", "repair", "surrogate_train", "groups", "scores"],
                     default="c1",
                     help="c1: 128x128x96 f32 (the headline); c2: 256x256x160 f16 graded mesh; "
                          "c4: 16 uneven f16 problems in one batched graph launch; "
@@ -787,6 +787,69 @@ def run_groups(args):
     return 0
 
 
+def run_scores(args):
+    """Registration scores of a population (the evaluation of Sec. 5) on the
+    128x128x96 problem with its five organ masks: per solution, the warped
+    label image of both sides and the Hausdorff distance and its 95th
+    percentile of every organ on each side (2 warps + 10 surface distances).
+    value = scored solutions per second."""
+    import torch
+    import synth
+    from paper_2303_04873_gb300 import build as _b
+    _b.build()
+    from paper_2303_04873_gb300 import morea
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    p = synth.make_c1(n_sol=32)
+    n = p.n_solutions
+    la, lb = synth.label_pair((p.nx, p.ny, p.nz), synth.phantom.C1_ELLIPSOIDS, 6.0)
+    lab = [torch.as_tensor(la).to(dev), torch.as_tensor(lb).to(dev)]
+    n_org = len(synth.phantom.C1_ELLIPSOIDS)
+    gp = morea.Problem(p, max_solutions=1)
+    S = torch.as_tensor(p.sol_src).to(dev)
+    T = torch.as_tensor(p.sol_tgt).to(dev)
+    work = torch.empty(morea.surface_distance_workspace(p.nx, p.ny, p.nz), dtype=torch.uint8, device=dev)
+    scores = torch.empty((n, 2, n_org, 4), dtype=torch.float64, device=dev)
+
+    def step_fn():
+        for i in range(n):
+            for side in (0, 1):
+                w = gp.warp_labels(S[i], T[i], side, lab[1 - side])
+                for o in range(n_org):
+                    morea.surface_distance(lab[side], w, o + 1, work=work, out=scores[i, side, o])
+
+    for _ in range(max(3, args.warmup)):
+        step_fn()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(0)
+    ms = []
+    for _ in range(args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step_fn()
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    ck = clocks.stop()
+    total = float(sum(ms))
+    hd = scores[..., 0].cpu().numpy()
+    line = {
+        "metric": "scored solutions/sec (warped organ masks, HD and HD95)", "value": n * args.steps / (total / 1e3),
+        "unit": "solutions/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total / args.steps, "higher_is_better": True, "data": "synthetic", "dtype": "int32 (exact)",
+        "config": {"workload": f"scores: 128x128x96, 2304 tets, {n} solutions, {n_org} organ masks; per solution "
+                               f"2 warped label images + {2 * n_org} surface distances"},
+        "hd_mean_voxels": float(np.nanmean(hd)),
+        # per solution and side: the warp kernel, then per organ 8 kernels (surface, x pass, 2 x 2
+        # line passes, directed distances, selection)
+        "gpu_launches": n * 2 * (1 + n_org * 8) * args.steps, "clocks": ck,
+    }
+    print(json.dumps(line), flush=True)
+    gp.close()
+    return 0
+
+
 def bf16_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -850,6 +913,8 @@ def main():
         return run_surrogate_train(args)
     if args.workload == "repair" and args.impl != "reference":
         return run_repair(args)
+    if args.workload == "scores" and args.impl != "reference":
+        return run_scores(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "c4":

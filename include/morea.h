@@ -366,6 +366,41 @@ morea_status morea_displacement(morea_problem *p, const float *src, const float 
                                 const uint8_t *labels_own, const uint8_t *labels_other, int32_t n_labels,
                                 int64_t *overlap, void *stream);
 
+/* Warped label image of one solution (the evaluation of Sec. 5).  For every
+ * voxel centre p of image `side` inside an unfolded copy of that side's mesh
+ * (the association of morea_displacement), warped(p) = labels_other at the
+ * voxel of the other image nearest to T(p) (round half to even, clamped);
+ * MOREA_NO_LABEL where no copy covers p.  src, tgt: device [V][3] FP32;
+ * labels_other, warped: device [nz][ny][nx] uint8 (caller-owned).  Compare
+ * warped with this side's own labels (morea_surface_distance) to score the
+ * registration.  MOREA_EINVAL: null pointers, side not 0/1. */
+#define MOREA_NO_LABEL 255
+morea_status morea_warp_labels(morea_problem *p, const float *src, const float *tgt, int32_t side,
+                               const uint8_t *labels_other, uint8_t *warped, void *stream);
+
+/* Bytes of device workspace morea_surface_distance needs for an
+ * nx x ny x nz image (0 if a size is out of range). */
+size_t morea_surface_distance_workspace(int32_t nx, int32_t ny, int32_t nz);
+
+/* Hausdorff distance and its 95th percentile between the surfaces of label
+ * `label` in two label images (the evaluation metrics of Sec. 5).
+ *   a, b     device [nz][ny][nx] uint8 label images; 1 <= nx, ny, nz <= 1024
+ *   label    0..255; a mask is the set of voxels equal to it
+ *   work     device workspace of morea_surface_distance_workspace() bytes
+ *            (caller-owned; its contents need not be preserved between calls)
+ *   out      device double[4]: HD, HD95 (voxel units), |S_a|, |S_b|
+ * The surface of a mask is its voxels with a face neighbour outside the
+ * mask (beyond the image border counts as outside).  The directed distances
+ * of S_a are the Euclidean distances from each of its voxel centres to the
+ * nearest voxel centre of S_b (exact: squared distances are integers), and
+ * likewise for S_b.  HD is the largest directed distance; HD95 the larger of
+ * the two directed 95th percentiles, each by nearest rank (the
+ * ceil(0.95 n)-th smallest).  An empty surface gives NaN for HD and HD95.
+ * Stream-ordered, no allocation, no host synchronisation.  MOREA_EINVAL:
+ * sizes out of range, null pointers, work_bytes too small. */
+morea_status morea_surface_distance(int32_t nx, int32_t ny, int32_t nz, const uint8_t *a, const uint8_t *b,
+                                    int32_t label, void *work, size_t work_bytes, double *out, void *stream);
+
 /* Read and clear the network's device status word (synchronises the
  * stream).  Bit 0 (MOREA_DEV_MLP_WAIT_TIMEOUT): a wait inside a
  * tensor-core product gave up (its outputs are invalid).  No counterpart in

@@ -2,7 +2,8 @@
 // evaluation of Sec. 5): for every voxel centre p of one image inside an
 // unfolded copy (exact association, reading R3), dvf(p) = T(p) - p with the
 // copy's FP32 affine map, and the label of the other image at the voxel
-// nearest to T(p) (round half to even, clamped) against the own label.
+// nearest to T(p) (round half to even, clamped), counted against the own
+// label and/or written out as the warped label image.
 //
 // One warp per tet: lane 0 builds the copy's rasterisation set-up in shared
 // memory, the lanes take the rows of its bounding box and walk their
@@ -23,13 +24,14 @@ __global__ void __launch_bounds__(kDvfWarps * 32) k_dvf(const DevProblem *__rest
                                                         const float *__restrict__ tgt, int side, float *__restrict__ dvf,
                                                         const uint8_t *__restrict__ lab_own,
                                                         const uint8_t *__restrict__ lab_oth, int n_labels,
-                                                        unsigned long long *__restrict__ counts)
+                                                        unsigned long long *__restrict__ counts,
+                                                        uint8_t *__restrict__ warped)
 {
     __shared__ RasterSetup sus[kDvfWarps];
     __shared__ unsigned long long hist[kMaxLabels][3];
     const DevProblem &P = *dp;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const bool labels = counts != nullptr;
+    const bool labels = counts != nullptr, pull = labels || warped != nullptr;
     for (int i = threadIdx.x; i < kMaxLabels * 3; i += blockDim.x) (&hist[0][0])[i] = 0ull;
     __syncthreads();
     RasterSetup &su = sus[warp];
@@ -69,12 +71,14 @@ __global__ void __launch_bounds__(kDvfWarps * 32) k_dvf(const DevProblem *__rest
                         dvf[3 * idx + 1] = yy - (float)j;
                         dvf[3 * idx + 2] = yz - (float)k;
                     }
-                    if (labels) {
+                    if (pull) {
                         const int mx = (int)fminf(fmaxf(rintf(yx), 0.0f), (float)(nx - 1));
                         const int my = (int)fminf(fmaxf(rintf(yy), 0.0f), (float)(ny - 1));
                         const int mz = (int)fminf(fmaxf(rintf(yz), 0.0f), (float)(nz - 1));
-                        const int la = lab_own[idx];
                         const int lb = lab_oth[((size_t)mz * ny + my) * nx + mx];
+                        if (warped) warped[idx] = (uint8_t)lb;
+                        if (!labels) continue;
+                        const int la = lab_own[idx];
                         if (la < n_labels) atomicAdd(&hist[la][0], 1ull);
                         if (lb < n_labels) atomicAdd(&hist[lb][1], 1ull);
                         if (la == lb && la < n_labels) atomicAdd(&hist[la][2], 1ull);
@@ -99,15 +103,16 @@ int dvf_max_labels() { return kMaxLabels; }
 
 cudaError_t launch_dvf(const DevProblem *dp, const DevProblem &hp, const float *src, const float *tgt, int side,
                        float *dvf, const uint8_t *lab_own, const uint8_t *lab_oth, int n_labels,
-                       unsigned long long *counts, cudaStream_t st)
+                       unsigned long long *counts, uint8_t *warped, cudaStream_t st)
 {
     const size_t N = (size_t)hp.nx * hp.ny * hp.nz;
     cudaError_t e = cudaSuccess;
     if (dvf) e = cudaMemsetAsync(dvf, 0xFF, 3 * N * sizeof(float), st);        // all-ones words are NaN
     if (e == cudaSuccess && counts) e = cudaMemsetAsync(counts, 0, 3 * (size_t)n_labels * sizeof(*counts), st);
+    if (e == cudaSuccess && warped) e = cudaMemsetAsync(warped, 0xFF, N, st);           // 255: in no copy
     if (e != cudaSuccess) return e;
     const int blocks = (int)std::min<long long>((hp.n_tets + kDvfWarps - 1) / kDvfWarps, 65535);
-    k_dvf<<<blocks, kDvfWarps * 32, 0, st>>>(dp, src, tgt, side, dvf, lab_own, lab_oth, n_labels, counts);
+    k_dvf<<<blocks, kDvfWarps * 32, 0, st>>>(dp, src, tgt, side, dvf, lab_own, lab_oth, n_labels, counts, warped);
     return cudaGetLastError();
 }
 

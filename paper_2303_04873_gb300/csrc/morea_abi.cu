@@ -512,7 +512,16 @@ morea_status morea_displacement(morea_problem *p, const float *src, const float 
     DeviceGuard g(p->device);
     return from_cuda(launch_dvf(p->dp, p->hp, src, tgt, side, dvf, labels ? labels_own : nullptr,
                                 labels ? labels_other : nullptr, labels ? n_labels : 0,
-                                labels ? reinterpret_cast<unsigned long long *>(overlap) : nullptr,
+                                labels ? reinterpret_cast<unsigned long long *>(overlap) : nullptr, nullptr,
+                                (cudaStream_t)stream));
+}
+
+morea_status morea_warp_labels(morea_problem *p, const float *src, const float *tgt, int32_t side,
+                               const uint8_t *labels_other, uint8_t *warped, void *stream)
+{
+    if (!p || !src || !tgt || (side != 0 && side != 1) || !labels_other || !warped) return MOREA_EINVAL;
+    DeviceGuard g(p->device);
+    return from_cuda(launch_dvf(p->dp, p->hp, src, tgt, side, nullptr, nullptr, labels_other, 0, nullptr, warped,
                                 (cudaStream_t)stream));
 }
 

@@ -165,7 +165,7 @@ cudaError_t launch_sample(const DevProblem *probs, const DevProblem &hp, const W
 int dvf_max_labels();
 cudaError_t launch_dvf(const DevProblem *dp, const DevProblem &hp, const float *src, const float *tgt, int side,
                        float *dvf, const uint8_t *lab_own, const uint8_t *lab_oth, int n_labels,
-                       unsigned long long *counts, cudaStream_t st);
+                       unsigned long long *counts, uint8_t *warped, cudaStream_t st);
 // Repair of folded solutions (k_repair.cu), one warp per solution.
 cudaError_t launch_repair(const DevProblem *dp, const DevProblem &hp, const int *v2t_off, const int *v2t_idx,
                           int n_sol, float *src, float *tgt, const float *noise, int max_points, double scale,

@@ -38,7 +38,7 @@ ENTRY_POINTS = (
     "morea_partial_features", "morea_mlp_create", "morea_mlp_destroy", "morea_mlp_info",
     "morea_mlp_set_params", "morea_mlp_get_params", "morea_mlp_forward", "morea_mlp_gradients",
     "morea_mlp_train_step", "morea_mlp_device_status", "morea_repair_folds", "morea_displacement",
-    "morea_parallel_groups",
+    "morea_parallel_groups", "morea_warp_labels", "morea_surface_distance_workspace", "morea_surface_distance",
     "morea_device_status", "morea_problem_info", "morea_batch_create", "morea_batch_destroy",
     "morea_batch_eval_full", "morea_batch_capture", "morea_batch_replay", "morea_set_launch",
     "morea_batch_set_launch", "morea_profile", "morea_profile_read", "morea_fold_magnitude_noalloc",
@@ -99,6 +99,9 @@ def lib():
     L.morea_repair_folds.argtypes = [vp, i32, vp, vp, vp, i32, ctypes.c_float, vp, vp, vp]
     L.morea_displacement.argtypes = [vp, vp, vp, i32, vp, vp, vp, i32, vp, vp]
     L.morea_parallel_groups.argtypes = [i32, i32, vp, i32, vp, vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    L.morea_warp_labels.argtypes = [vp, vp, vp, i32, vp, vp, vp]
+    L.morea_surface_distance_workspace.argtypes = [i32, i32, i32]
+    L.morea_surface_distance.argtypes = [i32, i32, i32, vp, vp, i32, vp, ctypes.c_size_t, vp, vp]
     L.morea_read_records.argtypes = [vp, i32, vp, vp, vp]
     L.morea_read_totals.argtypes = [vp, i32, vp, vp, vp]
     L.morea_device_status.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_uint32)]
@@ -130,8 +133,9 @@ def lib():
     L.morea_status_string.argtypes = [i32]
     L.morea_status_string.restype = ctypes.c_char_p
     for name in ENTRY_POINTS:
-        if name != "morea_status_string":
+        if name not in ("morea_status_string", "morea_surface_distance_workspace"):
             getattr(L, name).restype = ctypes.c_int
+    L.morea_surface_distance_workspace.restype = ctypes.c_size_t
     _lib = L
     return L
 
@@ -147,6 +151,37 @@ def parallel_groups(n_points: int, tets):
                                        el.ctypes.data_as(ctypes.c_void_p), grp.ctypes.data_as(ctypes.c_void_p),
                                        ctypes.byref(m), ctypes.byref(g)), "morea_parallel_groups")
     return el[:m.value].copy(), grp[:m.value].copy()
+
+
+NO_LABEL = 255
+
+
+def surface_distance_workspace(nx: int, ny: int, nz: int) -> int:
+    """Device bytes surface_distance needs for an nx x ny x nz image."""
+    n = int(lib().morea_surface_distance_workspace(int(nx), int(ny), int(nz)))
+    if n == 0:
+        raise MoreaError(EINVAL, "morea_surface_distance_workspace")
+    return n
+
+
+def surface_distance(a: torch.Tensor, b: torch.Tensor, label: int, work: Optional[torch.Tensor] = None,
+                     out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """Hausdorff distance, its 95th percentile (voxel units) and the two
+    surface sizes of label ``label`` in two device uint8 label images
+    [nz][ny][nx] (Sec. 5): a device float64 tensor [4] (``out`` if given,
+    contiguous).  ``work`` may be a reused device uint8 buffer of
+    surface_distance_workspace() bytes."""
+    nz, ny, nx = (int(x) for x in a.shape)
+    need = surface_distance_workspace(nx, ny, nz)
+    if work is None:
+        work = torch.empty((need,), dtype=torch.uint8, device=a.device)
+    if out is None:
+        out = torch.empty((4,), dtype=torch.float64, device=a.device)
+    _check(lib().morea_surface_distance(
+        nx, ny, nz, _dev(a, torch.uint8, (nz, ny, nx), "a"), _dev(b, torch.uint8, (nz, ny, nx), "b"), int(label),
+        _dev(work, torch.uint8, None, "work"), ctypes.c_size_t(work.numel()), _dev(out, torch.float64, (4,), "out"),
+        _stream(stream)), "morea_surface_distance")
+    return out
 
 
 def status_string(code: int) -> str:
@@ -357,6 +392,19 @@ class Problem:
             None if counts is None else _dev(counts, torch.int64, None, "overlap"), _stream(stream)),
             "morea_displacement")
         return dvf, counts
+
+    def warp_labels(self, src: torch.Tensor, tgt: torch.Tensor, side: int, labels_other: torch.Tensor,
+                    stream=None) -> torch.Tensor:
+        """Warped label image [nz][ny][nx] uint8 of one solution on image
+        ``side``: the other image's label at the voxel nearest to T(p);
+        NO_LABEL where no copy covers p."""
+        V = self.n_points
+        warped = torch.empty((self.nz, self.ny, self.nx), dtype=torch.uint8, device=src.device)
+        _check(self._L.morea_warp_labels(
+            self._h, _dev(src, torch.float32, (V, 3), "src"), _dev(tgt, torch.float32, (V, 3), "tgt"), int(side),
+            _dev(labels_other, torch.uint8, (self.nz, self.ny, self.nx), "labels_other"),
+            _dev(warped, torch.uint8, None, "warped"), _stream(stream)), "morea_warp_labels")
+        return warped
 
     def check_folds(self, src: torch.Tensor, tgt: torch.Tensor, stream=None):
         n = int(src.shape[0])

@@ -149,3 +149,25 @@ def test_null_handles_and_status_strings(mo):
     for code in range(7):
         assert mo.status_string(code) != "unknown status"
     assert mo.status_string(99) == "unknown status"
+
+
+def test_surface_distance_arguments_checked_on_host(mo):
+    L = mo.lib()
+    need = mo.surface_distance_workspace(128, 128, 96)
+    N = 128 * 128 * 96
+    bins = 127 ** 2 + 127 ** 2 + 95 ** 2 + 1
+    assert need >= N + 12 * N + 8 * bins
+    assert need % 256 == 0
+    assert L.morea_surface_distance_workspace(0, 4, 4) == 0
+    assert L.morea_surface_distance_workspace(1025, 4, 4) == 0
+    assert L.morea_surface_distance_workspace(1, 1, 1) > 0
+    fake = ctypes.c_void_p(256)        # never dereferenced: every call below fails its host checks
+    ok = (8, 8, 8, fake, fake, 1, fake, mo.surface_distance_workspace(8, 8, 8), fake, None)
+    for i, bad in ((0, 0), (1, 2000), (3, None), (4, None), (5, -1), (5, 256), (6, None), (8, None)):
+        args = list(ok)
+        args[i] = bad
+        assert L.morea_surface_distance(*args) == mo.EINVAL
+    args = list(ok)
+    args[7] = ok[7] - 1                # workspace one byte short
+    assert L.morea_surface_distance(*args) == mo.EINVAL
+    assert L.morea_warp_labels(None, fake, fake, 0, fake, fake, None) == mo.EINVAL
