@@ -128,6 +128,11 @@ def lib():
         L.orc_dvf.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
         L.orc_dvf.restype = ctypes.c_int
+        L.orc_gexp.argtypes = [ctypes.c_double]
+        L.orc_gexp.restype = ctypes.c_double
+        L.orc_init_noise.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                     ctypes.c_void_p, ctypes.c_int]
+        L.orc_init_noise.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -292,6 +297,17 @@ class Oracle:
             raise OracleError("oracle warp_labels failed")
         return warped
 
+    def init_noise(self, X, kernels, fixed=None, max_rounds: int = 20):
+        """R18: one mesh X [V][3] after the attraction rounds of the kernels
+        [K][5] = (cx, cy, cz, sigma, a); returns (X', rounds kept)."""
+        x = np.array(X, dtype=np.float32, copy=True, order="C")
+        k = np.ascontiguousarray(kernels, dtype=np.float32).reshape(-1, 5)
+        f = None if fixed is None else np.ascontiguousarray(fixed, dtype=np.uint8)
+        r = self._L.orc_init_noise(self._h, _ptr(x), _ptr(k), int(k.shape[0]), _ptr(f), int(max_rounds))
+        if r < 0:
+            raise OracleError("oracle init_noise failed")
+        return x, int(r)
+
     def repair_sigma(self, X, v: int, scale: float = 1.0) -> float:
         x = np.ascontiguousarray(X, dtype=np.float32)
         return float(self._L.orc_repair_sigma(self._h, _ptr(x), int(v), float(scale)))
@@ -313,6 +329,11 @@ class Oracle:
 
 
 # -- building blocks, exposed for the pins -----------------------------------
+
+def gexp(t: float) -> float:
+    """R18's exp for t <= 0 (range reduction by ln 2 + Taylor series)."""
+    return float(lib().orc_gexp(float(t)))
+
 
 def snap1(x: float, n: int, k: int) -> int:
     return int(lib().orc_snap1(ctypes.c_float(x), n, k))

@@ -94,6 +94,16 @@
  *      the integer (as R9); per label l the counts of covered voxels with
  *      own label l, with pulled-back label l, and with both.  The warped
  *      label image holds the pulled-back label per voxel, 255 in no copy.
+ *   R18 initialisation noise (Sec. 4.2.2, App. A.5: Gaussian kernels
+ *      on both images attract the mesh points, in rounds, as long as no
+ *      fold appears).  Per mesh, kernels (c_k, sigma_k, a_k) are the
+ *      caller's draws; a round moves x by sum_k a_k g_k(x) (c_k - x) with
+ *      g_k(x) = exp(-|c_k - x|^2 / (2 sigma_k^2)), in FP64 over k in order,
+ *      rounded to float, with fixed axes kept; it is kept if the moved
+ *      mesh has no folded tet, and the first folding round ends the
+ *      process.  exp is the function gexp below (range reduction by ln 2
+ *      and a Taylor series, every operation one rounded IEEE operation), so
+ *      positions are reproducible bit for bit.
  */
 #include <math.h>
 #include <stdint.h>
@@ -1053,4 +1063,71 @@ int orc_dvf(const orc_state *st, const float *src, const float *tgt, int side, d
     }
     free(covered);
     return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* R18: initialisation noise by Gaussian attraction kernels            */
+/* ------------------------------------------------------------------ */
+
+/* exp(t) for t <= 0 (R18): t = n ln2 + r with n = rint(t / ln2), exp(r) by
+ * its Taylor series to degree 13 in Horner form (s <- 1 + r s / k for
+ * k = 13 .. 1; the truncation is below 1e-17 relative for |r| <= ln2 / 2),
+ * then scaled by 2^n exactly.  Zero below -64.  Every operation is a single
+ * rounded IEEE operation (this file is compiled without contraction). */
+static double gexp(double t)
+{
+    const double LN2 = 0.6931471805599453;
+    if (!(t >= -64.0)) return 0.0;
+    double n = rint(t / LN2);
+    double r = t - n * LN2;
+    double s = 1.0;
+    for (int k = 13; k >= 1; --k) s = 1.0 + (r * s) / (double)k;
+    return ldexp(s, (int)n);
+}
+
+double orc_gexp(double t) { return gexp(t); }
+
+static int mesh_folded(const orc_state *st, const float *X)
+{
+    for (int t = 0; t < st->p.n_tets; ++t)
+        if (tet_folded(st, X, t)) return 1;
+    return 0;
+}
+
+/* One mesh X [V][3] (in/out) under K kernels [K][5] = (cx, cy, cz, sigma,
+ * a): a round moves every point x to x + sum_k a_k exp(-|c_k - x|^2 /
+ * (2 sigma_k^2)) (c_k - x), in FP64 over k in order, rounded to float;
+ * coordinates whose bit is set in fixed[v] (bit a = axis a) stay.  The
+ * round is kept if no tet of the moved mesh is folded (R2 on the snapped
+ * coordinates); the first round that folds ends the process.  Returns the
+ * number of kept rounds (<= max_rounds). */
+int orc_init_noise(const orc_state *st, float *X, const float *kernels, int K, const uint8_t *fixed, int max_rounds)
+{
+    const int V = st->p.n_points;
+    float *Y = (float *)malloc(sizeof(float) * 3 * (size_t)V);
+    if (!Y) return -1;
+    int kept = 0;
+    for (int round = 0; round < max_rounds; ++round) {
+        for (int v = 0; v < V; ++v) {
+            double x[3] = {X[3 * v], X[3 * v + 1], X[3 * v + 2]};
+            double d[3] = {0.0, 0.0, 0.0};
+            for (int k = 0; k < K; ++k) {
+                const float *c = kernels + 5 * k;
+                double dx = (double)c[0] - x[0], dy = (double)c[1] - x[1], dz = (double)c[2] - x[2];
+                double q = (dx * dx + dy * dy) + dz * dz;
+                double sig = c[3];
+                double w = (double)c[4] * gexp(-(q / (2.0 * (sig * sig))));
+                d[0] = d[0] + w * dx;
+                d[1] = d[1] + w * dy;
+                d[2] = d[2] + w * dz;
+            }
+            for (int a = 0; a < 3; ++a)
+                Y[3 * v + a] = (fixed && (fixed[v] >> a) & 1) ? X[3 * v + a] : (float)(x[a] + d[a]);
+        }
+        if (mesh_folded(st, Y)) break;
+        memcpy(X, Y, sizeof(float) * 3 * (size_t)V);
+        ++kept;
+    }
+    free(Y);
+    return kept;
 }
