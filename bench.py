@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--seeds", type=int, default=5, help="c3: EA seeds compared (200, 201, ...)")
     ap.add_argument("--estimator", choices=["voxels", "sampled"], default="voxels",
                     help="c1/c2: voxel centres (default) or the sampled estimator of App. A.2 (1 point per voxel^3)")
-    ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4", "repair", "surrogate_train", "groups", "scores"],
+    ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4", "repair", "surrogate_train", "groups", "scores", "init"],
                     default="c1",
                     help="c1: 128x128x96 f32 (the headline); c2: 256x256x160 f16 graded mesh; "
                          "c4: 16 uneven f16 problems in one batched graph launch; "
@@ -787,6 +787,69 @@ def run_groups(args):
     return 0
 
 
+def run_init(args):
+    """Initialisation noise (Sec. 4.2.2, App. A.5) for the 128x128x96
+    problem's population: 128 solutions start from the reference mesh and
+    8 Gaussian kernels per mesh (centres uniform in the image, sigma 8-24
+    voxels, strength 0.02-0.15) attract the points for up to 50 rounds while
+    the mesh stays unfolded.  value = initialised solutions per second."""
+    import torch
+    import synth
+    from paper_2303_04873_gb300 import build as _b
+    _b.build()
+    from paper_2303_04873_gb300 import morea
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    p = synth.make_c1()
+    n, K, R = p.n_solutions, 8, 50
+    rng = np.random.default_rng(11)
+    box = np.array([p.nx, p.ny, p.nz], np.float64) - 1
+    ker = np.concatenate([rng.uniform(0, 1, (n, 2, K, 3)) * box, rng.uniform(8, 24, (n, 2, K, 1)),
+                          rng.uniform(0.02, 0.15, (n, 2, K, 1))], -1).astype(np.float32)
+    f = p.fixed_axes.astype(np.uint8)
+    fixed = torch.as_tensor((f[:, 0] | (f[:, 1] << 1) | (f[:, 2] << 2)).astype(np.uint8)).to(dev)
+    ref = torch.as_tensor(np.broadcast_to(p.ref_points.astype(np.float32), (n, p.n_points, 3)).copy()).to(dev)
+    kd = torch.as_tensor(ker).to(dev)
+    gp = morea.Problem(p, max_solutions=1)
+    S, T = ref.clone(), ref.clone()
+    for _ in range(max(3, args.warmup)):
+        S.copy_(ref)
+        T.copy_(ref)
+        rounds = gp.init_noise(S, T, kd, R, fixed=fixed)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(0)
+    ms = []
+    for _ in range(args.steps):
+        S.copy_(ref)
+        T.copy_(ref)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        rounds = gp.init_noise(S, T, kd, R, fixed=fixed)
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    ck = clocks.stop()
+    total = float(sum(ms))
+    folded, _ = gp.check_folds(S, T)
+    r = rounds.float()
+    line = {
+        "metric": "initialised solutions/sec (Gaussian attraction noise)", "value": n * args.steps / (total / 1e3),
+        "unit": "solutions/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total / args.steps, "higher_is_better": True, "data": "synthetic",
+        "dtype": "f64 (explicitly rounded) / int64 (exact orientations)",
+        "config": {"workload": f"init: 128x128x96, 567 points, 2304 tets, {n} solutions x 2 meshes, {K} kernels "
+                               f"per mesh, up to {R} rounds"},
+        "rounds_mean": float(r.mean().item()), "rounds_min": int(rounds.min().item()),
+        "displacement_mean_voxels": float((torch.cat([S, T]) - ref.repeat(2, 1, 1)).norm(dim=-1).mean().item()),
+        "folded_after": int(folded.sum().item()),
+        "gpu_launches": args.steps, "clocks": ck,
+    }
+    print(json.dumps(line), flush=True)
+    gp.close()
+    return 0
+
+
 def run_scores(args):
     """Registration scores of a population (the evaluation of Sec. 5) on the
     128x128x96 problem with its five organ masks: per solution, the warped
@@ -915,6 +978,8 @@ def main():
         return run_repair(args)
     if args.workload == "scores" and args.impl != "reference":
         return run_scores(args)
+    if args.workload == "init" and args.impl != "reference":
+        return run_init(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "c4":

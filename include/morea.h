@@ -329,6 +329,31 @@ morea_status morea_mlp_info(const morea_mlp *n, int64_t *n_params, int32_t *padd
 morea_status morea_repair_folds(morea_problem *p, int32_t n_sol, float *src, float *tgt, const float *noise,
                                 int32_t max_points, float scale, int32_t *moved, double *severity, void *stream);
 
+/* Initialisation noise for a diverse initial population (Sec. 4.2.2,
+ * App. A.5): Gaussian kernels on both images attract the mesh points in
+ * rounds while the mesh stays unfolded.
+ *   src, tgt  device [n_sol][V][3] FP32, in: the start meshes (e.g. copies
+ *             of the reference mesh), out: the result
+ *   fixed     device [V] uint8 or NULL; bit a set: axis a of that point does
+ *             not move (points on the faces of the image box)
+ *   kernels   device [n_sol][2][n_kernels][5] FP32 (cx, cy, cz, sigma, a) for
+ *             the source (0) and target (1) mesh of each solution: the
+ *             caller's random draws, centres in voxel units, sigma > 0
+ *   rounds    device [n_sol][2] int32: the rounds kept for each mesh
+ * A round moves every point x to x + sum_k a_k exp(-|c_k - x|^2 /
+ * (2 sigma_k^2)) (c_k - x), computed in FP64 over k in order with each
+ * operation rounded once, and rounded to FP32; the round is kept if no tet
+ * of the moved mesh is folded (exact orientation of the snapped
+ * coordinates) and the first round that folds ends the process, so the
+ * result is never folded.  At most max_rounds rounds.  Points are not
+ * clamped (the snap clamps them at evaluation); with sum_k a_k <= 1 they
+ * stay inside the convex hull of the start mesh and the centres.
+ * MOREA_EINVAL: null pointers, n_sol < 1, n_kernels < 0, max_rounds < 0,
+ * or more than 200 KiB of shared memory (5 n_kernels + 6 V floats). */
+morea_status morea_init_noise(morea_problem *p, int32_t n_sol, float *src, float *tgt, const uint8_t *fixed,
+                              int32_t n_kernels, const float *kernels, int32_t max_rounds, int32_t *rounds,
+                              void *stream);
+
 /* Linkage model and parallel groups of the partial evaluations (Sec. 4.2.1).
  * Host call; needs no GPU.  tets: host [n_tets][4] topology.  The FOS
  * elements are mesh edges chosen by a greedy set cover of the points (the

@@ -525,6 +525,19 @@ morea_status morea_warp_labels(morea_problem *p, const float *src, const float *
                                 (cudaStream_t)stream));
 }
 
+morea_status morea_init_noise(morea_problem *p, int32_t n_sol, float *src, float *tgt, const uint8_t *fixed,
+                              int32_t n_kernels, const float *kernels, int32_t max_rounds, int32_t *rounds,
+                              void *stream)
+{
+    if (!p || n_sol < 1 || n_sol > (1 << 29) || !src || !tgt || n_kernels < 0 || (n_kernels > 0 && !kernels) ||
+        max_rounds < 0 || !rounds)
+        return MOREA_EINVAL;
+    if (init_smem_bytes(p->V, n_kernels) > 200 * 1024) return MOREA_EINVAL;
+    DeviceGuard g(p->device);
+    return from_cuda(launch_init(p->dp, p->hp, n_sol, src, tgt, fixed, n_kernels, kernels, max_rounds, rounds,
+                                 (cudaStream_t)stream));
+}
+
 morea_status morea_repair_folds(morea_problem *p, int32_t n_sol, float *src, float *tgt, const float *noise,
                                 int32_t max_points, float scale, int32_t *moved, double *severity, void *stream)
 {

@@ -162,6 +162,10 @@ cudaError_t launch_sample(const DevProblem *probs, const DevProblem &hp, const W
                           const RasterSetup *setup, RasterOut *rout, const int *n_entries_dev, int n_entries_host,
                           int grid, int chunk, int *queue, cudaStream_t st);
 // Displacement field and label overlap of one solution (k_dvf.cu).
+size_t init_smem_bytes(int n_points, int n_kernels);
+cudaError_t launch_init(const DevProblem *dp, const DevProblem &hp, int n_sol, float *src, float *tgt,
+                        const uint8_t *fixed, int n_kernels, const float *kernels, int max_rounds, int *rounds,
+                        cudaStream_t st);
 int dvf_max_labels();
 cudaError_t launch_dvf(const DevProblem *dp, const DevProblem &hp, const float *src, const float *tgt, int side,
                        float *dvf, const uint8_t *lab_own, const uint8_t *lab_oth, int n_labels,

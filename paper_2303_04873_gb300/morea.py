@@ -38,7 +38,7 @@ ENTRY_POINTS = (
     "morea_partial_features", "morea_mlp_create", "morea_mlp_destroy", "morea_mlp_info",
     "morea_mlp_set_params", "morea_mlp_get_params", "morea_mlp_forward", "morea_mlp_gradients",
     "morea_mlp_train_step", "morea_mlp_device_status", "morea_repair_folds", "morea_displacement",
-    "morea_parallel_groups", "morea_warp_labels", "morea_surface_distance_workspace", "morea_surface_distance",
+    "morea_parallel_groups", "morea_init_noise", "morea_warp_labels", "morea_surface_distance_workspace", "morea_surface_distance",
     "morea_device_status", "morea_problem_info", "morea_batch_create", "morea_batch_destroy",
     "morea_batch_eval_full", "morea_batch_capture", "morea_batch_replay", "morea_set_launch",
     "morea_batch_set_launch", "morea_profile", "morea_profile_read", "morea_fold_magnitude_noalloc",
@@ -100,6 +100,7 @@ def lib():
     L.morea_displacement.argtypes = [vp, vp, vp, i32, vp, vp, vp, i32, vp, vp]
     L.morea_parallel_groups.argtypes = [i32, i32, vp, i32, vp, vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
     L.morea_warp_labels.argtypes = [vp, vp, vp, i32, vp, vp, vp]
+    L.morea_init_noise.argtypes = [vp, i32, vp, vp, vp, i32, vp, i32, vp, vp]
     L.morea_surface_distance_workspace.argtypes = [i32, i32, i32]
     L.morea_surface_distance.argtypes = [i32, i32, i32, vp, vp, i32, vp, ctypes.c_size_t, vp, vp]
     L.morea_read_records.argtypes = [vp, i32, vp, vp, vp]
@@ -392,6 +393,21 @@ class Problem:
             None if counts is None else _dev(counts, torch.int64, None, "overlap"), _stream(stream)),
             "morea_displacement")
         return dvf, counts
+
+    def init_noise(self, src: torch.Tensor, tgt: torch.Tensor, kernels: torch.Tensor, max_rounds: int,
+                   fixed: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        """Gaussian-attraction initialisation noise (Sec. 4.2.2), in place on
+        src, tgt [n][V][3]; kernels [n][2][K][5] = (cx, cy, cz, sigma, a);
+        fixed [V] uint8 axis bits.  Returns the rounds kept, [n][2] int32."""
+        n = int(src.shape[0])
+        V = self.n_points
+        K = int(kernels.shape[2])
+        rounds = torch.empty((n, 2), dtype=torch.int32, device=src.device)
+        _check(self._L.morea_init_noise(
+            self._h, n, _dev(src, torch.float32, (n, V, 3), "src"), _dev(tgt, torch.float32, (n, V, 3), "tgt"),
+            _dev(fixed, torch.uint8, (V,), "fixed"), K, _dev(kernels, torch.float32, (n, 2, K, 5), "kernels"),
+            int(max_rounds), _dev(rounds, torch.int32, (n, 2), "rounds"), _stream(stream)), "morea_init_noise")
+        return rounds
 
     def warp_labels(self, src: torch.Tensor, tgt: torch.Tensor, side: int, labels_other: torch.Tensor,
                     stream=None) -> torch.Tensor:
