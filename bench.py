@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--seeds", type=int, default=5, help="c3: EA seeds compared (200, 201, ...)")
     ap.add_argument("--estimator", choices=["voxels", "sampled"], default="voxels",
                     help="c1/c2: voxel centres (default) or the sampled estimator of App. A.2 (1 point per voxel^3)")
-    ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4", "repair", "surrogate_train", "groups", "scores", "init"],
+    ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4", "repair", "surrogate_train", "groups", "scores", "init", "gomea"],
                     default="c1",
                     help="c1: 128x128x96 f32 (the headline); c2: 256x256x160 f16 graded mesh; "
                          "c4: 16 uneven f16 problems in one batched graph launch; "
@@ -787,6 +787,62 @@ def run_groups(args):
     return 0
 
 
+def run_gomea(args):
+    """MO-RV-GOMEA generations (Sec. 3, 4.2-4.3) on the 128x128x96 problem:
+    population 128 from the initialisation noise, 10 clusters, the edge FOS
+    in its DSATUR parallel groups; each generation clusters the population
+    (host), and per group samples one request per (solution, element) from
+    its cluster's distribution (device), evaluates them in one batched
+    partial evaluation (device), accepts (host) and commits (device).
+    Wall-clock time with the device synchronised around each generation.
+    value = partial evaluations per second."""
+    import time
+    import torch
+    import synth
+    from paper_2303_04873_gb300 import build as _b
+    _b.build()
+    from paper_2303_04873_gb300 import morea, gomea
+    torch.cuda.set_device(0)
+    p = synth.make_c1(n_sol=1)
+    n = 128
+    gp = morea.Problem(p, max_solutions=n, max_requests=gomea.max_requests(p, n), max_changed=2)
+    run = gomea.Gomea(gp, p, n, gomea.GomeaConfig(), seed=1)
+    ref = 1.1 * run.obj.max(axis=0)
+    hv0 = run.hypervolume(ref)
+    for _ in range(max(3, args.warmup)):
+        run.step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    ms, reqs, accs = [], 0, 0
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = run.step()
+        torch.cuda.synchronize()
+        ms.append((time.perf_counter() - t0) * 1e3)
+        reqs += st["requests"]
+        accs += st["accepted"]
+    ck = clocks.stop()
+    total = float(sum(ms))
+    assert gp.device_status() == 0
+    line = {
+        "metric": "partial evaluations/sec (MO-RV-GOMEA generations)", "value": reqs / (total / 1e3),
+        "unit": "partial-evals/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total / args.steps, "higher_is_better": True, "data": "synthetic", "dtype": "f32/f64",
+        "config": {"workload": f"gomea: 128x128x96 f32, 2304 tets, population {n}, 10 clusters, "
+                               f"{len(run.groups)} parallel groups of {len(run.el_host)} edge elements; "
+                               f"one step = one generation (wall clock, host work included)"},
+        "requests_per_generation": reqs / args.steps, "accepted_per_generation": accs / args.steps,
+        "hv_start": hv0, "hv_end": run.hypervolume(ref), "archive": int(len(run.archive.pts)),
+        # per group: sampling (2 kernels), partial evaluation (entries, entry work, image pass, guidance,
+        # finalize), commit, slot objectives
+        "gpu_launches": 9 * len(run.groups) * args.steps, "clocks": ck,
+    }
+    print(json.dumps(line), flush=True)
+    gp.close()
+    return 0
+
+
 def run_init(args):
     """Initialisation noise (Sec. 4.2.2, App. A.5) for the 128x128x96
     problem's population: 128 solutions start from the reference mesh and
@@ -980,6 +1036,8 @@ def main():
         return run_scores(args)
     if args.workload == "init" and args.impl != "reference":
         return run_init(args)
+    if args.workload == "gomea" and args.impl != "reference":
+        return run_gomea(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "c4":

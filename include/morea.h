@@ -329,6 +329,71 @@ morea_status morea_mlp_info(const morea_mlp *n, int64_t *n_params, int32_t *padd
 morea_status morea_repair_folds(morea_problem *p, int32_t n_sol, float *src, float *tgt, const float *noise,
                                 int32_t max_points, float scale, int32_t *moved, double *severity, void *stream);
 
+/* Objectives of committed slots (a9 from the slots' running totals, which
+ * morea_eval_full and morea_commit_partial keep up to date): obj device
+ * [n_sol][3], folded device [n_sol], severity device [n_sol] or NULL, as
+ * morea_eval_full returns them.  slot: device [n_sol] or NULL (identity).
+ * A slot out of range gets NaN objectives and folded = 1.  MOREA_EINVAL:
+ * null p/obj/folded, n_sol < 1. */
+morea_status morea_slot_objectives(morea_problem *p, int32_t n_sol, const int32_t *slot, double *obj,
+                                   uint8_t *folded, double *severity, void *stream);
+
+/* Selection and clustering of MO-RV-GOMEA (Sec. 3).  Host call; needs no
+ * GPU.  obj: host [n][3] objectives of the population (finite).  The
+ * population is ranked into non-dominated fronts; the ceil(tau n)
+ * solutions first in (rank, index) order are selected; objectives are
+ * scaled by the selection's range per objective; k leaders are chosen by
+ * farthest-first traversal (from the smallest scaled f_0; ties to the
+ * lower index); balanced k-means keeps, per cluster, the c = min(|S|,
+ * ceil(2 |S| / k)) selected solutions nearest to its mean (ties to the
+ * lower index), for at most `iters` rounds or until memberships repeat;
+ * every population member is assigned to the nearest mean (ties to the
+ * lower cluster).  Squared distances are summed in axis order and nothing
+ * is contracted, so results are reproducible bit for bit.
+ * Outputs (host): *n_selected and selected [n] (first *n_selected valid);
+ * *cluster_size = c and members [k][n] (row q: the c population indices of
+ * cluster q, in selection order); pop_cluster [n].  Clusters may overlap.
+ * MOREA_EINVAL: n < 1, k < 1, iters < 1, tau not in (0, 1], a non-finite
+ * objective, null pointers. */
+morea_status morea_cluster(int32_t n, const double *obj, double tau, int32_t k, int32_t iters,
+                           int32_t *n_selected, int32_t *selected, int32_t *cluster_size, int32_t *members,
+                           int32_t *pop_cluster);
+
+/* Bytes of device workspace morea_sample_elements needs (0 if a count is
+ * below 1): one model (12 means + a 12 x 12 factor, FP64) per (cluster,
+ * element). */
+size_t morea_sample_elements_workspace(int32_t n_clusters, int32_t n_elements);
+
+/* Distributions of the FOS elements per cluster and new partial solutions
+ * drawn from them (Sec. 3, optimal mixing).  An element (a, b) has 12
+ * variables: source a (x, y, z), source b, target a, target b; variables
+ * on a fixed axis of their point keep the parent's value.
+ *   src, tgt     device [n_pop][V][3] FP32: the population's coordinates
+ *   members      device [n_clusters][cluster_size] population indices
+ *   elements     device [n_elements][2] point pairs, 8-byte aligned
+ *   fixed        device [V] uint8 axis bits, or NULL
+ *   cmult        device [n_clusters] distribution multipliers
+ *   req_sol, req_cluster, req_element  device [n_req]: parent, cluster and
+ *                element of each new partial solution
+ *   z            device [n_req][12] standard normal draws (the caller's)
+ *   work         device workspace of morea_sample_elements_workspace()
+ *                bytes (caller-owned, not preserved between calls)
+ *   new_src, new_tgt  device [n_req][2][3]: the new coordinates of points a
+ *                and b of each request: the candidate rows of a
+ *                morea_eval_partial request whose changed points are (a, b)
+ * Per (cluster, element): mu = the members' mean (summed in member order),
+ * Sigma = the maximum-likelihood covariance, L = the Cholesky factor of
+ * Sigma + 1e-6 I over the free variables, all FP64; a request draws
+ * mu + cmult L z, rounded to FP32.  An index out of range yields NaN rows.
+ * Stream-ordered, no allocation.  MOREA_EINVAL: null pointers, counts out of
+ * range, misaligned elements, work_bytes too small. */
+morea_status morea_sample_elements(morea_problem *p, int32_t n_pop, const float *src, const float *tgt,
+                                   int32_t n_clusters, int32_t cluster_size, const int32_t *members,
+                                   int32_t n_elements, const int32_t *elements, const uint8_t *fixed,
+                                   const float *cmult, int32_t n_req, const int32_t *req_sol,
+                                   const int32_t *req_cluster, const int32_t *req_element, const float *z,
+                                   void *work, size_t work_bytes, float *new_src, float *new_tgt, void *stream);
+
 /* Initialisation noise for a diverse initial population (Sec. 4.2.2,
  * App. A.5): Gaussian kernels on both images attract the mesh points in
  * rounds while the mesh stays unfolded.

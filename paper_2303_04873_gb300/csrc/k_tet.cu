@@ -517,6 +517,23 @@ __global__ void k_gather_totals(const morea_totals *__restrict__ tot, int max_so
     if (s >= 0 && s < max_sol) out[i] = tot[s];
 }
 
+// Objectives of committed slots from their running totals (a9).
+__global__ void k_slot_objectives(const DevProblem *__restrict__ dp, int n_sol, const int *__restrict__ slot,
+                                  double *obj, uint8_t *folded, double *severity)
+{
+    const DevProblem &P = *dp;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_sol) return;
+    const int s = slot ? slot[i] : i;
+    if (s < 0 || s >= P.max_sol) {
+        bad_outputs(obj + 3 * i, folded + i, severity ? severity + i : nullptr);
+        return;
+    }
+    const morea_totals t = P.totals[s];
+    const Acc a = {t.s_img, t.s_guid, t.s_mag, t.n_vox, t.n_gp, t.n_folded, t.sev};
+    objectives(P, a, obj + 3 * i, folded + i, severity ? severity + i : nullptr);
+}
+
 // Distance map of each contour group (Sec. 4.1.3 / App. A.3): Euclidean
 // distance from each voxel centre to the nearest point of the group, and the
 // per-voxel mask of groups whose truncation band (distance < r) holds it.
@@ -795,6 +812,13 @@ cudaError_t launch_gather_totals(const DevProblem &hp, int n_sol, const int *slo
                                  cudaStream_t st)
 {
     k_gather_totals<<<(n_sol + kBlock - 1) / kBlock, kBlock, 0, st>>>(hp.totals, hp.max_sol, n_sol, slot, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_slot_objectives(const DevProblem *dp, int n_sol, const int *slot, double *obj, uint8_t *folded,
+                                  double *severity, cudaStream_t st)
+{
+    k_slot_objectives<<<(n_sol + kBlock - 1) / kBlock, kBlock, 0, st>>>(dp, n_sol, slot, obj, folded, severity);
     return cudaGetLastError();
 }
 

@@ -525,6 +525,39 @@ morea_status morea_warp_labels(morea_problem *p, const float *src, const float *
                                 (cudaStream_t)stream));
 }
 
+morea_status morea_slot_objectives(morea_problem *p, int32_t n_sol, const int32_t *slot, double *obj,
+                                   uint8_t *folded, double *severity, void *stream)
+{
+    if (!p || n_sol < 1 || !obj || !folded) return MOREA_EINVAL;
+    DeviceGuard g(p->device);
+    return from_cuda(launch_slot_objectives(p->dp, n_sol, slot, obj, folded, severity, (cudaStream_t)stream));
+}
+
+size_t morea_sample_elements_workspace(int32_t n_clusters, int32_t n_elements)
+{
+    if (n_clusters < 1 || n_elements < 1) return 0;
+    return sample_elements_bytes(n_clusters, n_elements);
+}
+
+morea_status morea_sample_elements(morea_problem *p, int32_t n_pop, const float *src, const float *tgt,
+                                   int32_t n_clusters, int32_t cluster_size, const int32_t *members,
+                                   int32_t n_elements, const int32_t *elements, const uint8_t *fixed,
+                                   const float *cmult, int32_t n_req, const int32_t *req_sol,
+                                   const int32_t *req_cluster, const int32_t *req_element, const float *z,
+                                   void *work, size_t work_bytes, float *new_src, float *new_tgt, void *stream)
+{
+    if (!p || n_pop < 1 || !src || !tgt || n_clusters < 1 || cluster_size < 1 || !members || n_elements < 1 ||
+        !elements || !cmult || n_req < 0 || !work)
+        return MOREA_EINVAL;
+    if (n_req > 0 && (!req_sol || !req_cluster || !req_element || !z || !new_src || !new_tgt)) return MOREA_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(elements) & 7) != 0) return MOREA_EINVAL;
+    if (work_bytes < sample_elements_bytes(n_clusters, n_elements)) return MOREA_EINVAL;
+    DeviceGuard g(p->device);
+    return from_cuda(launch_sample_elements(p->V, n_pop, src, tgt, n_clusters, cluster_size, members, n_elements,
+                                            elements, fixed, cmult, n_req, req_sol, req_cluster, req_element, z,
+                                            work, new_src, new_tgt, (cudaStream_t)stream));
+}
+
 morea_status morea_init_noise(morea_problem *p, int32_t n_sol, float *src, float *tgt, const uint8_t *fixed,
                               int32_t n_kernels, const float *kernels, int32_t max_rounds, int32_t *rounds,
                               void *stream)

@@ -162,6 +162,14 @@ cudaError_t launch_sample(const DevProblem *probs, const DevProblem &hp, const W
                           const RasterSetup *setup, RasterOut *rout, const int *n_entries_dev, int n_entries_host,
                           int grid, int chunk, int *queue, cudaStream_t st);
 // Displacement field and label overlap of one solution (k_dvf.cu).
+cudaError_t launch_slot_objectives(const DevProblem *dp, int n_sol, const int *slot, double *obj, uint8_t *folded,
+                                  double *severity, cudaStream_t st);
+size_t sample_elements_bytes(int n_clusters, int n_elements);
+cudaError_t launch_sample_elements(int V, int n_pop, const float *src, const float *tgt, int C, int csize,
+                                   const int *members, int m, const int *elements, const uint8_t *fixed,
+                                   const float *cmult, int n_req, const int *req_sol, const int *req_cluster,
+                                   const int *req_elem, const float *z, void *work, float *new_src, float *new_tgt,
+                                   cudaStream_t st);
 size_t init_smem_bytes(int n_points, int n_kernels);
 cudaError_t launch_init(const DevProblem *dp, const DevProblem &hp, int n_sol, float *src, float *tgt,
                         const uint8_t *fixed, int n_kernels, const float *kernels, int max_rounds, int *rounds,

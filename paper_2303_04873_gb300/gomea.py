@@ -1,0 +1,185 @@
+"""MO-RV-GOMEA generations as MOREA runs them (Sec. 3, Sec. 4.2-4.3), driven
+from the host over the library's device calls.
+
+A generation:
+  1. selection and balanced clustering of the population in objective space
+     (``morea.cluster``, host);
+  2. for every parallel group of FOS elements (mesh edges from a greedy set
+     cover, coloured by DSATUR, ``morea.parallel_groups``): one request per
+     (solution, element of the group), drawn from the distribution of that
+     element in the solution's cluster (``Problem.sample_elements``,
+     device), all evaluated by one batched partial evaluation (device);
+  3. a request is accepted if its partial solution is unfolded and dominates
+     its parent or is not dominated by the elitist archive (Sec. 3); under
+     adaptive steering its f_guidance must also stay within the window
+     (Sec. 4.3.2); accepted requests are committed (device) and the
+     solutions' objectives re-read from the committed totals (device);
+  4. the archive takes the new solutions; the distribution multiplier of a
+     cluster grows by 10 % after a generation with an accepted request of
+     that cluster and shrinks by 10 % otherwise, within [0.1, 10]
+     (reading R20); from the steering generation on the archive keeps only
+     f_guidance in [s_G, factor s_G] (reading R21).
+
+The initial population comes from ``Problem.init_noise`` (Sec. 4.2.2).
+Folded candidates are discarded (Sec. 4.3.1: the default without repair).
+"""
+
+from __future__ import annotations
+
+import dataclasses
+from typing import List, Optional
+
+import numpy as np
+import torch
+
+from . import morea
+from .ea import Archive, hv3d
+
+
+@dataclasses.dataclass
+class GomeaConfig:
+    tau: float = 0.35                # selection fraction
+    clusters: int = 10               # the paper's runs use 10 clusters
+    kmeans_iters: int = 10
+    archive_cap: int = 2000          # the paper's archive capacity
+    steer_at: int = 100              # adaptive steering from this generation on
+    steer_factor: float = 1.5
+    cmult0: float = 1.0
+    init_kernels: int = 8            # Gaussian kernels per mesh for the initial noise
+    init_rounds: int = 50
+    init_sigma: tuple = (8.0, 24.0)
+    init_strength: tuple = (0.02, 0.15)
+
+
+def fixed_bits(fixed_axes: np.ndarray) -> np.ndarray:
+    f = np.asarray(fixed_axes, bool).astype(np.uint8)
+    return (f[:, 0] | (f[:, 1] << 1) | (f[:, 2] << 2)).astype(np.uint8)
+
+
+def max_requests(prob, n_pop: int) -> int:
+    """The request capacity a Problem needs for Gomea: one request per
+    (solution, element) of the largest parallel group."""
+    _, grp = morea.parallel_groups(prob.n_points, prob.tets)
+    return int(n_pop) * int(np.bincount(grp).max())
+
+
+class Gomea:
+    """``gp`` must hold at least n_pop slots, max_requests(prob, n_pop)
+    requests and 2 changed points per request."""
+
+    def __init__(self, gp: "morea.Problem", prob, n_pop: int, cfg: Optional[GomeaConfig] = None, seed: int = 0,
+                 start_src: Optional[np.ndarray] = None, start_tgt: Optional[np.ndarray] = None):
+        self.gp, self.cfg = gp, cfg or GomeaConfig()
+        self.rng = np.random.default_rng(seed)
+        self.dev = torch.device("cuda")
+        self.n, self.V = int(n_pop), prob.n_points
+        el, grp = morea.parallel_groups(prob.n_points, prob.tets)
+        self.elements = torch.as_tensor(el).to(self.dev).contiguous()
+        self.el_host = el
+        self.groups = [np.nonzero(grp == g)[0].astype(np.int32) for g in range(int(grp.max()) + 1)]
+        self.fixed = torch.as_tensor(fixed_bits(prob.fixed_axes)).to(self.dev)
+        # initial population: the reference mesh with Gaussian-attraction noise
+        if start_src is None:
+            ref = np.broadcast_to(prob.ref_points.astype(np.float32), (self.n, self.V, 3)).copy()
+            S = torch.as_tensor(ref).to(self.dev)
+            T = S.clone()
+            c = self.cfg
+            box = np.array([prob.nx, prob.ny, prob.nz], np.float64) - 1
+            K = c.init_kernels
+            ker = np.concatenate([self.rng.uniform(0, 1, (self.n, 2, K, 3)) * box,
+                                  self.rng.uniform(*c.init_sigma, (self.n, 2, K, 1)),
+                                  self.rng.uniform(*c.init_strength, (self.n, 2, K, 1))], -1).astype(np.float32)
+            gp.init_noise(S, T, torch.as_tensor(ker).to(self.dev), c.init_rounds, fixed=self.fixed)
+        else:
+            S = torch.as_tensor(np.ascontiguousarray(start_src, np.float32)).to(self.dev)
+            T = torch.as_tensor(np.ascontiguousarray(start_tgt, np.float32)).to(self.dev)
+        self.S, self.T = S, T
+        obj, folded, _ = gp.eval_full(S, T)
+        self.obj = obj.cpu().numpy()
+        self.folded = folded.cpu().numpy().astype(bool)
+        self.archive = Archive(self.cfg.archive_cap)
+        for i in range(self.n):
+            if not self.folded[i]:
+                self.archive.add(self.obj[i])
+        self.cmult = np.full(self.cfg.clusters, self.cfg.cmult0, np.float64)
+        self.generation_index = 0
+        self.requests = 0
+        self.accepted = 0
+        self.work = None
+
+    def steering(self) -> bool:
+        return self.generation_index >= self.cfg.steer_at
+
+    def window_hi(self) -> float:
+        if len(self.archive.pts) == 0:
+            return np.inf
+        return self.cfg.steer_factor * float(self.archive.pts[:, 2].min())
+
+    def _archive_accepts(self, o: np.ndarray, chunk: int = 2048) -> np.ndarray:
+        """Per row of o: no archived point is at least as good in every objective."""
+        a = self.archive.pts
+        out = np.ones(len(o), bool)
+        if len(a) == 0:
+            return out
+        for s in range(0, len(o), chunk):
+            out[s:s + chunk] = ~np.any(np.all(a[None, :, :] <= o[s:s + chunk, None, :], axis=2), axis=1)
+        return out
+
+    def step(self) -> dict:
+        """One generation; returns its counts."""
+        c = self.cfg
+        _, members, pop_cluster = morea.cluster(self.obj, c.tau, c.clusters, c.kmeans_iters)
+        mem_d = torch.as_tensor(members).to(self.dev).contiguous()
+        cm_d = torch.as_tensor(self.cmult.astype(np.float32)).to(self.dev)
+        hit = np.zeros(c.clusters, bool)
+        n_req_total = n_acc_total = 0
+        steer = self.steering()
+        for grp in self.groups:
+            m = len(grp)
+            req_sol = np.repeat(np.arange(self.n, dtype=np.int32), m)
+            req_el = np.tile(grp, self.n).astype(np.int32)
+            req_cl = pop_cluster[req_sol].astype(np.int32)
+            n_req = len(req_sol)
+            z = self.rng.standard_normal((n_req, 12)).astype(np.float32)
+            d = [torch.as_tensor(a).to(self.dev) for a in (req_sol, req_cl, req_el, z)]
+            new_s, new_t = self.gp.sample_elements(self.S, self.T, mem_d, self.elements, cm_d, d[0], d[1], d[2], d[3],
+                                                   fixed=self.fixed, work=self.work)
+            off = torch.arange(0, 2 * n_req + 1, 2, dtype=torch.int32, device=self.dev)
+            pts = self.elements[d[2].long()].reshape(-1).contiguous()
+            o, f, _ = self.gp.eval_partial(d[0], off, pts, new_s, new_t)
+            o = o.cpu().numpy()
+            f = f.cpu().numpy().astype(bool)
+            hi = self.window_hi() if steer else np.inf
+            ok = ~f & np.all(np.isfinite(o), axis=1) & (o[:, 2] <= hi)
+            par = self.obj[req_sol]
+            better = np.all(o <= par, axis=1) & np.any(o < par, axis=1)
+            acc = (ok & (better | self._archive_accepts(o))).astype(np.uint8)
+            self.gp.commit_partial(torch.as_tensor(acc).to(self.dev))
+            if acc.any():
+                rows = torch.as_tensor(np.nonzero(acc)[0]).to(self.dev)
+                sol = d[0][rows].long()
+                ab = self.elements[d[2][rows].long()].long()
+                for j in range(2):
+                    self.S[sol, ab[:, j]] = new_s.view(n_req, 2, 3)[rows, j]
+                    self.T[sol, ab[:, j]] = new_t.view(n_req, 2, 3)[rows, j]
+                changed = np.unique(req_sol[acc.astype(bool)])
+                obj, folded, _ = self.gp.slot_objectives(self.n)
+                obj = obj.cpu().numpy()
+                for i in changed:
+                    self.obj[i] = obj[i]
+                    self.archive.add(self.obj[i])
+                hit[np.unique(req_cl[acc.astype(bool)])] = True
+            n_req_total += n_req
+            n_acc_total += int(acc.sum())
+        self.cmult = np.where(hit, np.minimum(self.cmult * 1.1, 10.0), np.maximum(self.cmult * 0.9, 0.1))
+        self.generation_index += 1
+        if self.steering() and len(self.archive.pts):
+            pts = self.archive.pts
+            s_g = float(pts[:, 2].min())
+            self.archive.pts = pts[pts[:, 2] <= c.steer_factor * s_g]
+        self.requests += n_req_total
+        self.accepted += n_acc_total
+        return {"requests": n_req_total, "accepted": n_acc_total}
+
+    def hypervolume(self, ref) -> float:
+        return hv3d(self.archive.pts, ref)

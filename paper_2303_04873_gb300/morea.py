@@ -38,7 +38,8 @@ ENTRY_POINTS = (
     "morea_partial_features", "morea_mlp_create", "morea_mlp_destroy", "morea_mlp_info",
     "morea_mlp_set_params", "morea_mlp_get_params", "morea_mlp_forward", "morea_mlp_gradients",
     "morea_mlp_train_step", "morea_mlp_device_status", "morea_repair_folds", "morea_displacement",
-    "morea_parallel_groups", "morea_init_noise", "morea_warp_labels", "morea_surface_distance_workspace", "morea_surface_distance",
+    "morea_parallel_groups", "morea_init_noise", "morea_warp_labels", "morea_cluster", "morea_slot_objectives",
+    "morea_sample_elements_workspace", "morea_sample_elements", "morea_surface_distance_workspace", "morea_surface_distance",
     "morea_device_status", "morea_problem_info", "morea_batch_create", "morea_batch_destroy",
     "morea_batch_eval_full", "morea_batch_capture", "morea_batch_replay", "morea_set_launch",
     "morea_batch_set_launch", "morea_profile", "morea_profile_read", "morea_fold_magnitude_noalloc",
@@ -101,6 +102,12 @@ def lib():
     L.morea_parallel_groups.argtypes = [i32, i32, vp, i32, vp, vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
     L.morea_warp_labels.argtypes = [vp, vp, vp, i32, vp, vp, vp]
     L.morea_init_noise.argtypes = [vp, i32, vp, vp, vp, i32, vp, i32, vp, vp]
+    L.morea_cluster.argtypes = [i32, vp, ctypes.c_double, i32, i32, ctypes.POINTER(i32), vp, ctypes.POINTER(i32),
+                                vp, vp]
+    L.morea_slot_objectives.argtypes = [vp, i32, vp, vp, vp, vp, vp]
+    L.morea_sample_elements_workspace.argtypes = [i32, i32]
+    L.morea_sample_elements.argtypes = [vp, i32, vp, vp, i32, i32, vp, i32, vp, vp, vp, i32, vp, vp, vp, vp, vp,
+                                        ctypes.c_size_t, vp, vp, vp]
     L.morea_surface_distance_workspace.argtypes = [i32, i32, i32]
     L.morea_surface_distance.argtypes = [i32, i32, i32, vp, vp, i32, vp, ctypes.c_size_t, vp, vp]
     L.morea_read_records.argtypes = [vp, i32, vp, vp, vp]
@@ -134,9 +141,11 @@ def lib():
     L.morea_status_string.argtypes = [i32]
     L.morea_status_string.restype = ctypes.c_char_p
     for name in ENTRY_POINTS:
-        if name not in ("morea_status_string", "morea_surface_distance_workspace"):
+        if name not in ("morea_status_string", "morea_surface_distance_workspace",
+                        "morea_sample_elements_workspace"):
             getattr(L, name).restype = ctypes.c_int
     L.morea_surface_distance_workspace.restype = ctypes.c_size_t
+    L.morea_sample_elements_workspace.restype = ctypes.c_size_t
     _lib = L
     return L
 
@@ -155,6 +164,22 @@ def parallel_groups(n_points: int, tets):
 
 
 NO_LABEL = 255
+
+
+def cluster(obj, tau: float = 0.35, k: int = 10, iters: int = 10):
+    """Selection and balanced clustering of MO-RV-GOMEA (Sec. 3; host call).
+    Returns (selected indices, members [k][c] population indices, cluster of
+    every population member)."""
+    o = np.ascontiguousarray(obj, dtype=np.float64)
+    n = int(o.shape[0])
+    sel = np.zeros(n, np.int32)
+    mem = np.zeros((int(k), n), np.int32)
+    pc = np.zeros(n, np.int32)
+    ns, c = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().morea_cluster(n, o.ctypes.data_as(ctypes.c_void_p), float(tau), int(k), int(iters), ctypes.byref(ns),
+                               sel.ctypes.data_as(ctypes.c_void_p), ctypes.byref(c), mem.ctypes.data_as(ctypes.c_void_p),
+                               pc.ctypes.data_as(ctypes.c_void_p)), "morea_cluster")
+    return sel[:ns.value].copy(), mem[:, :c.value].copy(), pc
 
 
 def surface_distance_workspace(nx: int, ny: int, nz: int) -> int:
@@ -393,6 +418,46 @@ class Problem:
             None if counts is None else _dev(counts, torch.int64, None, "overlap"), _stream(stream)),
             "morea_displacement")
         return dvf, counts
+
+    def slot_objectives(self, n: int, slots: Optional[torch.Tensor] = None, stream=None):
+        """(obj [n][3], folded [n], severity [n]) of committed slots (device)."""
+        dev = torch.device("cuda")
+        obj = torch.empty((n, 3), dtype=torch.float64, device=dev)
+        folded = torch.empty((n,), dtype=torch.uint8, device=dev)
+        sev = torch.empty((n,), dtype=torch.float64, device=dev)
+        _check(self._L.morea_slot_objectives(
+            self._h, int(n), _dev(slots, torch.int32, (n,), "slots"), _dev(obj, torch.float64, (n, 3), "obj"),
+            _dev(folded, torch.uint8, (n,), "folded"), _dev(sev, torch.float64, (n,), "severity"), _stream(stream)),
+            "morea_slot_objectives")
+        return obj, folded, sev
+
+    def sample_elements(self, src: torch.Tensor, tgt: torch.Tensor, members: torch.Tensor, elements: torch.Tensor,
+                        cmult: torch.Tensor, req_sol: torch.Tensor, req_cluster: torch.Tensor,
+                        req_element: torch.Tensor, z: torch.Tensor, fixed: Optional[torch.Tensor] = None,
+                        work: Optional[torch.Tensor] = None, stream=None):
+        """New coordinates (new_src, new_tgt [n_req*2][3]) of the two points of
+        each requested FOS element, drawn from its cluster's distribution
+        (Sec. 3).  src, tgt [n_pop][V][3]; members [k][c]; elements [m][2]."""
+        n_pop, V = int(src.shape[0]), self.n_points
+        k, c = (int(x) for x in members.shape)
+        m = int(elements.shape[0])
+        n_req = int(req_sol.shape[0])
+        need = int(self._L.morea_sample_elements_workspace(k, m))
+        if work is None or work.numel() < need:
+            work = torch.empty((need,), dtype=torch.uint8, device=src.device)
+        new_s = torch.empty((2 * n_req, 3), dtype=torch.float32, device=src.device)
+        new_t = torch.empty((2 * n_req, 3), dtype=torch.float32, device=src.device)
+        _check(self._L.morea_sample_elements(
+            self._h, n_pop, _dev(src, torch.float32, (n_pop, V, 3), "src"),
+            _dev(tgt, torch.float32, (n_pop, V, 3), "tgt"), k, c, _dev(members, torch.int32, (k, c), "members"), m,
+            _dev(elements, torch.int32, (m, 2), "elements"), _dev(fixed, torch.uint8, (V,), "fixed"),
+            _dev(cmult, torch.float32, (k,), "cmult"), n_req, _dev(req_sol, torch.int32, (n_req,), "req_sol"),
+            _dev(req_cluster, torch.int32, (n_req,), "req_cluster"),
+            _dev(req_element, torch.int32, (n_req,), "req_element"), _dev(z, torch.float32, (n_req, 12), "z"),
+            _dev(work, torch.uint8, None, "work"), ctypes.c_size_t(work.numel()),
+            _dev(new_s, torch.float32, None, "new_src"), _dev(new_t, torch.float32, None, "new_tgt"),
+            _stream(stream)), "morea_sample_elements")
+        return new_s, new_t
 
     def init_noise(self, src: torch.Tensor, tgt: torch.Tensor, kernels: torch.Tensor, max_rounds: int,
                    fixed: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
