@@ -27,7 +27,7 @@ Folded candidates are discarded (Sec. 4.3.1: the default without repair).
 from __future__ import annotations
 
 import dataclasses
-from typing import List, Optional
+from typing import Optional
 
 import numpy as np
 import torch
@@ -105,7 +105,8 @@ class Gomea:
         self.generation_index = 0
         self.requests = 0
         self.accepted = 0
-        self.work = None
+        self.work = torch.empty((morea.sample_elements_workspace(self.cfg.clusters, len(el)),), dtype=torch.uint8,
+                                device=self.dev)
 
     def steering(self) -> bool:
         return self.generation_index >= self.cfg.steer_at

@@ -166,6 +166,14 @@ def parallel_groups(n_points: int, tets):
 NO_LABEL = 255
 
 
+def sample_elements_workspace(n_clusters: int, n_elements: int) -> int:
+    """Device bytes Problem.sample_elements needs for its models."""
+    n = int(lib().morea_sample_elements_workspace(int(n_clusters), int(n_elements)))
+    if n == 0:
+        raise MoreaError(EINVAL, "morea_sample_elements_workspace")
+    return n
+
+
 def cluster(obj, tau: float = 0.35, k: int = 10, iters: int = 10):
     """Selection and balanced clustering of MO-RV-GOMEA (Sec. 3; host call).
     Returns (selected indices, members [k][c] population indices, cluster of
@@ -442,9 +450,8 @@ class Problem:
         k, c = (int(x) for x in members.shape)
         m = int(elements.shape[0])
         n_req = int(req_sol.shape[0])
-        need = int(self._L.morea_sample_elements_workspace(k, m))
-        if work is None or work.numel() < need:
-            work = torch.empty((need,), dtype=torch.uint8, device=src.device)
+        if work is None:
+            work = torch.empty((sample_elements_workspace(k, m),), dtype=torch.uint8, device=src.device)
         new_s = torch.empty((2 * n_req, 3), dtype=torch.float32, device=src.device)
         new_t = torch.empty((2 * n_req, 3), dtype=torch.float32, device=src.device)
         _check(self._L.morea_sample_elements(
