@@ -183,18 +183,24 @@ __global__ void __launch_bounds__(kBlock, 6) k_raster(const DevProblem *__restri
                                       : trilin_quad(oq, nx, ny, nz, yx, yy, yz);
                 kadd(s_img, c_img, hfun<HMODE>(a, b));
             };
-            // voxels [wbase, wbase + w) of the stream, one per lane.  The row of
-            // the window's first voxel is `head`; the later rows that start
-            // inside the window set bit (start - wbase) of `starts`, so a
-            // lane's row is head + popc(starts & bits <= its position).
-            auto window = [&](int wbase, int w) {
+            // voxels [wbase, wbase + w) of the stream, one per lane.  `head` is
+            // the last row starting at or before wbase (a row that starts
+            // exactly at wbase may follow it when it was appended after the
+            // previous window); the later rows that start inside the window
+            // set bit (start - wbase) of `starts`, so a lane's row is
+            // head + popc(starts & bits <= its position).  The return value
+            // counts the rows starting at or before wbase + 32: how far
+            // `head` moves for the next full window.
+            auto window = [&](int wbase, int w) -> int {
                 const int r = head + 1 + lane;
                 unsigned bit = 0u;
+                int st = 0x7fffffff;
                 if (r < tail) {
-                    const int st = Q.start[r & (kRowQ - 1)];
+                    st = Q.start[r & (kRowQ - 1)];
                     if (st < wbase + 32) bit = 1u << (st - wbase);
                 }
                 const unsigned starts = __reduce_or_sync(FULL, bit);
+                const unsigned done = __ballot_sync(FULL, st <= wbase + 32);
                 const int q = (head + __popc(starts & upto)) & (kRowQ - 1);
                 if (lane < w) {
                     const int2 db = Q.db[q];
@@ -203,16 +209,7 @@ __global__ void __launch_bounds__(kBlock, 6) k_raster(const DevProblem *__restri
                     voxel(wbase + lane, db.x, db.y, r.x, r.y, r.z, mc.x, mc.y, mc.z, mc.w);
                 }
                 __syncwarp();
-            };
-            // drop rows whose voxels all precede pend
-            auto advance = [&]() {
-                for (;;) {
-                    const int i = head + 1 + lane;
-                    const bool done = i < tail && Q.start[i & (kRowQ - 1)] <= pend;
-                    const unsigned bm = __ballot_sync(FULL, done);
-                    head += __popc(bm);
-                    if (bm != FULL) break;
-                }
+                return __popc(done);
             };
             // Rows of the bounding box that can meet the copy, 32 z-slices at
             // a time: lane l finds the y-extent [jl, jl + ns) of slice
@@ -296,9 +293,8 @@ __global__ void __launch_bounds__(kBlock, 6) k_raster(const DevProblem *__restri
                     total += batch_total;
                     __syncwarp();
                     while (total - pend >= kWin) {
-                        window(pend, kWin);
+                        head += window(pend, kWin);
                         pend += kWin;
-                        advance();
                     }
                 }
             }

@@ -50,6 +50,17 @@ def test_random_masks(mo, shape, seed):
     check(mo, b, a, 3)
 
 
+@pytest.mark.parametrize("shape", [(2, 3, 1024), (2, 1024, 3), (1024, 2, 3)])
+def test_maximum_line_lengths(mo, shape):
+    """Lines of 1024 voxels along each axis: 32 chunks in the x pass, and
+    128 KiB of staged column in the y and z passes."""
+    rng = np.random.default_rng(sum(shape))
+    a = (rng.random(shape) < 0.02).astype(np.uint8)
+    b = (rng.random(shape) < 0.01).astype(np.uint8)
+    check(mo, a, b, 1)
+    check(mo, a, b, 0)
+
+
 def test_hand_cases(mo):
     a = np.zeros((1, 1, 41), np.uint8)
     a[0, 0, 2:41:2] = 1
