@@ -11,7 +11,7 @@
 // morea_batch_set_launch, normally chosen by the autotuner).
 struct MoreaLaunch {
     int blocks_per_sm = 8;   // grid = blocks_per_sm x SM count
-    int chunk = 0;           // 0: static striding of items over warps; > 0: warps take
+    int chunk = 1;           // 0: static striding of items over warps; > 0: warps take
                              // `chunk` items at a time from an atomic queue
 };
 
