@@ -394,20 +394,52 @@ def run_ours(args):
     dR = [{k: torch.empty_like(v) for k, v in q.items()} for q in R]
     dA = [torch.empty_like(a) for a in A]
 
+    # Copies run on a side stream, pipelined with the evaluation: the inputs of
+    # partial round r land while the full evaluation and the earlier rounds
+    # run, and each round's outputs are read back while later rounds run.
+    # The step ends when its last copy has landed.
+    copy_stream = torch.cuda.Stream(device=dev)
+
     def e2e_step():
-        d_src.copy_(h_src, non_blocking=True)
-        d_tgt.copy_(h_tgt, non_blocking=True)
-        for q, hq in zip(dR, hR):
-            for k in q:
-                q[k].copy_(hq[k], non_blocking=True)
-        for a, ha in zip(dA, hA):
-            a.copy_(ha, non_blocking=True)
-        step(d_src, d_tgt, dR, dA)
-        for h, d in zip(h_out_full, out_full):
-            h.copy_(d, non_blocking=True)
-        for ho, do in zip(h_out_part, out_part):
-            for h, d in zip(ho, do):
+        go = torch.cuda.Event()
+        go.record(stream)
+        ev_in = []
+        with torch.cuda.stream(copy_stream):
+            copy_stream.wait_event(go)
+            d_src.copy_(h_src, non_blocking=True)
+            d_tgt.copy_(h_tgt, non_blocking=True)
+            ev_in.append(torch.cuda.Event())
+            ev_in[-1].record(copy_stream)
+        stream.wait_event(ev_in[0])
+        gp.eval_full(d_src, d_tgt, out=out_full, stream=stream)
+        with torch.cuda.stream(copy_stream):      # issued after the full evaluation, so it starts at once
+            for q, hq, a_, ha in zip(dR, hR, dA, hA):
+                for k in q:
+                    q[k].copy_(hq[k], non_blocking=True)
+                a_.copy_(ha, non_blocking=True)
+                ev_in.append(torch.cuda.Event())
+                ev_in[-1].record(copy_stream)
+        outs = [(out_full, h_out_full)]
+        for r in range(ROUNDS):
+            ev_out = torch.cuda.Event()
+            ev_out.record(stream)
+            with torch.cuda.stream(copy_stream):
+                copy_stream.wait_event(ev_out)
+                for h, d in zip(*outs[-1][::-1]):
+                    h.copy_(d, non_blocking=True)
+            stream.wait_event(ev_in[r + 1])
+            q = dR[r]
+            gp.eval_partial(q["slot"], q["chg_off"], q["chg_pts"], q["chg_src"], q["chg_tgt"], out=out_part[r],
+                            stream=stream)
+            gp.commit_partial(dA[r], stream=stream)
+            outs.append((out_part[r], h_out_part[r]))
+        ev_out = torch.cuda.Event()
+        ev_out.record(stream)
+        with torch.cuda.stream(copy_stream):
+            copy_stream.wait_event(ev_out)
+            for h, d in zip(*outs[-1][::-1]):
                 h.copy_(d, non_blocking=True)
+        stream.wait_stream(copy_stream)
 
     for _ in range(max(1, args.warmup)):
         e2e_step()
