@@ -87,20 +87,24 @@ Layout layout(int nx, int ny, int nz)
     return L;
 }
 
+// One warp per 32-voxel chunk of an image row: lanes along x (coalesced);
+// the chunk's row and z-plane are found once per warp.
 __global__ void k_surface(int nx, int ny, int nz, const uint8_t *__restrict__ a, const uint8_t *__restrict__ b,
                           int label, uint8_t *__restrict__ surf, Counters *ctr)
 {
-    const long long N = (long long)nx * ny * nz;
     const int lane = threadIdx.x & 31;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long w0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); w0 < N; w0 += stride) {
-        const long long v = w0 + lane;
+    const int cpr = (nx + 31) / 32;                           // chunks per row
+    const long long chunks = (long long)cpr * ny * nz;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    const long long sy = nx, sz = (long long)nx * ny;
+    for (long long wc = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); wc < chunks; wc += warps) {
+        const int c = (int)(wc % cpr);
+        const int row = (int)(wc / cpr);                      // k * ny + j
+        const int j = row % ny, k = row / ny;
+        const int i = c * 32 + lane;
+        const long long v = (long long)row * nx + i;
         unsigned bits = 0;
-        if (v < N) {
-            const int i = (int)(v % nx);
-            const int j = (int)((v / nx) % ny);
-            const int k = (int)(v / ((long long)nx * ny));
-            const long long sy = nx, sz = (long long)nx * ny;
+        if (i < nx) {
             const uint8_t *m[2] = {a, b};
 #pragma unroll
             for (int s = 0; s < 2; ++s) {
@@ -116,25 +120,20 @@ __global__ void k_surface(int nx, int ny, int nz, const uint8_t *__restrict__ a,
         const unsigned ca = __popc(__ballot_sync(FULL, bits & 1u));
         const unsigned cb = __popc(__ballot_sync(FULL, bits & 2u));
         if (ca | cb) {
-            unsigned c[3] = {0u, 0u, 0u};
-            if (bits) {
-                c[0] = (unsigned)(v % nx);
-                c[1] = (unsigned)((v / nx) % ny);
-                c[2] = (unsigned)(v / ((long long)nx * ny));
-            }
+            const unsigned c3[3] = {(unsigned)i, (unsigned)j, (unsigned)k};
 #pragma unroll
             for (int ax = 0; ax < 3; ++ax) {
-                const unsigned li = __reduce_max_sync(FULL, bits ? (unsigned)kMaxExtent - c[ax] : 0u);
-                const unsigned hp = __reduce_max_sync(FULL, bits ? c[ax] + 1u : 0u);
+                const unsigned li = __reduce_max_sync(FULL, bits ? (unsigned)kMaxExtent - c3[ax] : 0u);
+                const unsigned hp = __reduce_max_sync(FULL, bits ? c3[ax] + 1u : 0u);
                 if (lane == 0) {
                     atomicMax(&ctr->lo_inv[ax], li);
                     atomicMax(&ctr->hi_p1[ax], hp);
                 }
             }
-        }
-        if (lane == 0) {
-            if (ca) atomicAdd(&ctr->n[0], (unsigned long long)ca);
-            if (cb) atomicAdd(&ctr->n[1], (unsigned long long)cb);
+            if (lane == 0) {
+                if (ca) atomicAdd(&ctr->n[0], (unsigned long long)ca);
+                if (cb) atomicAdd(&ctr->n[1], (unsigned long long)cb);
+            }
         }
     }
 }
@@ -353,7 +352,9 @@ extern "C" morea_status morea_surface_distance(int32_t nx, int32_t ny, int32_t n
     cudaError_t e = cudaMemsetAsync(w + Lo.hist, 0, Lo.total - Lo.hist, st);   // histograms + counters
     if (e != cudaSuccess) return MOREA_ECUDA;
     const int blocks = (int)std::min<long long>((N + 255) / 256, 152LL * 8);
-    k_surface<<<blocks, 256, 0, st>>>(nx, ny, nz, a, b, label, surf, ctr);
+    const long long chunks = (long long)((nx + 31) / 32) * ny * nz;
+    k_surface<<<(int)std::min<long long>((chunks + 7) / 8, 152LL * 16), 256, 0, st>>>(nx, ny, nz, a, b, label, surf,
+                                                                                     ctr);
     const int row_blocks = (int)std::min<long long>(((long long)ny * nz + 7) / 8, 152LL * 16);
     k_edt_x<<<row_blocks, 256, 0, st>>>(nx, ny, nz, surf, ctr, fa, fb);
     if ((e = cudaGetLastError()) != cudaSuccess) return MOREA_ECUDA;

@@ -77,6 +77,8 @@ class Gomea:
         self.elements = torch.as_tensor(el).to(self.dev).contiguous()
         self.el_host = el
         self.groups = [np.nonzero(grp == g)[0].astype(np.int32) for g in range(int(grp.max()) + 1)]
+        # each group's element pairs on the device: the models are estimated per group
+        self.group_el = [torch.as_tensor(el[g]).to(self.dev).contiguous() for g in self.groups]
         self.fixed = torch.as_tensor(fixed_bits(prob.fixed_axes)).to(self.dev)
         # initial population: the reference mesh with Gaussian-attraction noise
         if start_src is None:
@@ -105,7 +107,8 @@ class Gomea:
         self.generation_index = 0
         self.requests = 0
         self.accepted = 0
-        self.work = torch.empty((morea.sample_elements_workspace(self.cfg.clusters, len(el)),), dtype=torch.uint8,
+        biggest = max(len(g) for g in self.groups)
+        self.work = torch.empty((morea.sample_elements_workspace(self.cfg.clusters, biggest),), dtype=torch.uint8,
                                 device=self.dev)
 
     def steering(self) -> bool:
@@ -135,18 +138,18 @@ class Gomea:
         hit = np.zeros(c.clusters, bool)
         n_req_total = n_acc_total = 0
         steer = self.steering()
-        for grp in self.groups:
+        for grp, gel in zip(self.groups, self.group_el):
             m = len(grp)
             req_sol = np.repeat(np.arange(self.n, dtype=np.int32), m)
-            req_el = np.tile(grp, self.n).astype(np.int32)
+            req_el = np.tile(np.arange(m, dtype=np.int32), self.n)          # index into this group's elements
             req_cl = pop_cluster[req_sol].astype(np.int32)
             n_req = len(req_sol)
             z = self.rng.standard_normal((n_req, 12)).astype(np.float32)
             d = [torch.as_tensor(a).to(self.dev) for a in (req_sol, req_cl, req_el, z)]
-            new_s, new_t = self.gp.sample_elements(self.S, self.T, mem_d, self.elements, cm_d, d[0], d[1], d[2], d[3],
+            new_s, new_t = self.gp.sample_elements(self.S, self.T, mem_d, gel, cm_d, d[0], d[1], d[2], d[3],
                                                    fixed=self.fixed, work=self.work)
             off = torch.arange(0, 2 * n_req + 1, 2, dtype=torch.int32, device=self.dev)
-            pts = self.elements[d[2].long()].reshape(-1).contiguous()
+            pts = gel[d[2].long()].reshape(-1).contiguous()
             o, f, _ = self.gp.eval_partial(d[0], off, pts, new_s, new_t)
             o = o.cpu().numpy()
             f = f.cpu().numpy().astype(bool)
@@ -159,7 +162,7 @@ class Gomea:
             if acc.any():
                 rows = torch.as_tensor(np.nonzero(acc)[0]).to(self.dev)
                 sol = d[0][rows].long()
-                ab = self.elements[d[2][rows].long()].long()
+                ab = gel[d[2][rows].long()].long()
                 for j in range(2):
                     self.S[sol, ab[:, j]] = new_s.view(n_req, 2, 3)[rows, j]
                     self.T[sol, ab[:, j]] = new_t.view(n_req, 2, 3)[rows, j]
