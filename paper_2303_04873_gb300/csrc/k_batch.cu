@@ -45,8 +45,11 @@ __global__ void __launch_bounds__(kBlock) k_batch_entries(const DevProblem *__re
         const int pi = find_prob(tb, e, [](const BatchProb &b) { return b.entry_off; });
         const DevProblem &P = probs[pi];
         const long long local = e - tb.p[pi].entry_off;
-        const int T = P.n_tets, V = P.n_points;
-        const int i = (int)(local / T), t = (int)(local - (long long)i * T);
+        const int V = P.n_points;
+        // tet-major within the problem (as k_full_entries): neighbouring
+        // items share a region of the images
+        const int ns = tb.p[pi].n_sol;
+        const int t = (int)(local / ns), i = (int)(local - (long long)t * ns);
         const int4 tv = P.tets[t];
         const int4 *sq = P.slot_q + (size_t)i * 2 * V;
         WorkEntry we;
@@ -98,7 +101,7 @@ __global__ void __launch_bounds__(kBlock) k_batch_reduce(const DevProblem *__res
     unsigned long long sev = 0;
     morea_tet_record *cache = P.cache + (size_t)i * T;
     for (int t = threadIdx.x; t < T; t += kBlock) {
-        const size_t e = (size_t)bp.entry_off + (size_t)i * T + t;
+        const size_t e = (size_t)bp.entry_off + (size_t)t * bp.n_sol + i;
         const TetOut to = tout[e];
         const RasterOut r0 = rout[2 * e], r1 = rout[2 * e + 1];
         morea_tet_record rec;

@@ -79,7 +79,10 @@ __global__ void __launch_bounds__(kBlock) k_full_entries(const DevProblem *__res
     const long long total = (long long)n_sol * T;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(e / T), t = (int)(e - (long long)i * T);
+        // tet-major: the copies of one tet in all solutions are neighbours in
+        // the work list, so the image pass works on one region of the images
+        // at a time and they stay in L2 across solutions
+        const int t = (int)(e / n_sol), i = (int)(e - (long long)t * n_sol);
         int s = slot ? slot[i] : i;
         const bool bad = s < 0 || s >= P.max_sol;
         if (bad) s = 0;
@@ -209,7 +212,7 @@ __global__ void __launch_bounds__(kBlock) k_reduce_full(const DevProblem *__rest
     Acc a = {0.0, 0.0, 0.0, 0, 0, 0, 0};
     morea_tet_record *cache = P.cache + (size_t)s * T;
     for (int t = threadIdx.x; t < T; t += kBlock) {
-        const size_t e = (size_t)i * T + t;
+        const size_t e = (size_t)t * n_sol + i;          // tet-major entries (k_full_entries)
         morea_tet_record rec = make_record(tout[e], rout[2 * e], rout[2 * e + 1]);
         cache[t] = rec;
         acc_add(a, rec, 1);
