@@ -121,7 +121,7 @@ def lib():
         L.orc_copy_shifts.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
         L.orc_sample_lambda.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]
         L.orc_repair.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
-                                 ctypes.c_double, ctypes.POINTER(ctypes.c_uint64)]
+                                 ctypes.c_double, ctypes.POINTER(ctypes.c_uint64), ctypes.c_void_p]
         L.orc_repair.restype = ctypes.c_int
         L.orc_repair_sigma.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double]
         L.orc_repair_sigma.restype = ctypes.c_double
@@ -252,15 +252,17 @@ class Oracle:
         self._L.orc_eval_tet(self._h, _ptr(src), _ptr(tgt), int(t), _ptr(rec))
         return rec[0]
 
-    def repair(self, src, tgt, noise, max_points: int, scale: float = 1.0):
-        """Repair (R14) of one solution; returns (src, tgt, moved, severity)."""
+    def repair(self, src, tgt, noise, max_points: int, scale: float = 1.0, fixed=None):
+        """Repair (R14) of one solution; returns (src, tgt, moved, severity).
+        fixed: optional [V] uint8 axis bits of coordinates that stay."""
         s = np.array(src, dtype=np.float32, copy=True, order="C")
         t = np.array(tgt, dtype=np.float32, copy=True, order="C")
         z = np.ascontiguousarray(noise, dtype=np.float32)
         assert z.size >= max_points * 64 * 3
+        fx = None if fixed is None else np.ascontiguousarray(fixed, dtype=np.uint8)
         sev = ctypes.c_uint64(0)
         moved = self._L.orc_repair(self._h, _ptr(s), _ptr(t), _ptr(z), int(max_points), float(scale),
-                                   ctypes.byref(sev))
+                                   ctypes.byref(sev), _ptr(fx))
         if moved < 0:
             raise OracleError("oracle repair failed")
         S = float(1 << int(self._P.subvoxel_bits))

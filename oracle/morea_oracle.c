@@ -82,7 +82,9 @@
  *      over its folded tets; ties to the lowest k) replaces x; if no trial
  *      decreases it, the repair of the solution stops.  At most max_points
  *      visits per solution.  FP64 without contraction, so the float trial
- *      positions are the same on every machine.
+ *      positions are the same on every machine.  With fixed axes given (bit
+ *      a of fixed[v]: axis a of point v lies on a face of the image box and
+ *      stays there), a trial keeps those coordinates of x.
  *   R15 displacement field and label overlap (the evaluation of Sec. 5):
  *      for every voxel centre p of one image inside an unfolded copy (R3),
  *      dvf(p) = T(p) - p with the FP64 barycentric map; voxels in no copy
@@ -921,7 +923,7 @@ static int tet_folded(const orc_state *st, const float *X, int t)
  * normal draws.  Returns the number of moved points; *sev_raw = sum of
  * |orient| over the folded copies of both meshes afterwards. */
 int orc_repair(const orc_state *st, float *src, float *tgt, const float *noise, int max_points, double scale,
-               uint64_t *sev_raw)
+               uint64_t *sev_raw, const uint8_t *fixed)
 {
     const orc_problem *P = &st->p;
     int moved = 0, visits = 0, stop = 0;
@@ -946,6 +948,10 @@ int orc_repair(const orc_state *st, float *src, float *tgt, const float *noise, 
                     const float *z = noise + ((size_t)visits * 64 + k) * 3;
                     float q[3];
                     for (int a = 0; a < 3; ++a) {
+                        if (fixed && ((fixed[v] >> a) & 1)) {      /* a fixed axis keeps its value */
+                            q[a] = X[3 * (size_t)v + a];
+                            continue;
+                        }
                         double step = sigma * (double)z[a];
                         double pos = (double)X[3 * (size_t)v + a] + step;
                         q[a] = (float)pos;

@@ -85,3 +85,41 @@ def test_random_meshes_never_get_worse(seed):
         if not before["folded"]:
             assert moved == 0
             np.testing.assert_array_equal(s, s0)
+
+
+def test_fixed_axes_stay_in_every_trial():
+    # the same inversion as above; with x and z of vertex 0 fixed, the kept
+    # trial moves only y: the best trial is the one whose y step undoes the
+    # fold, whatever its x and z draws are
+    folded = CORNER.copy()
+    folded[0] = BASE + np.array([1.0, 10.0, 1.0], np.float32)    # x + y + z = 12 > 8: inverted
+    orc = _orc(folded)
+    sigma = orc.repair_sigma(folded, 0, 1.0)
+    noise = np.zeros((2, 64, 3), np.float32)
+    noise[0, 3] = np.array([-40.0, -9.0, -40.0]) / sigma         # y back to 1; x, z would leave the box
+    fixed = np.zeros(4, np.uint8)
+    fixed[0] = 1 | 4                                             # x and z of vertex 0
+    s, t, moved, sev = orc.repair(folded, CORNER, noise, max_points=2, fixed=fixed)
+    assert moved == 1 and sev == 0.0
+    y = (np.float64(folded[0, 1]) + np.float64(sigma) * np.float64(noise[0, 3, 1])).astype(np.float32)
+    np.testing.assert_array_equal(s[0], [folded[0, 0], y, folded[0, 2]])
+    # without the fixed axes the same draw moves x and z as well
+    s2, _, _, _ = orc.repair(folded, CORNER, noise, max_points=2)
+    assert s2[0, 0] != folded[0, 0] and s2[0, 2] != folded[0, 2]
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_fixed_boundary_axes_on_random_meshes(seed):
+    from test_gpu_parity import _random_case
+    p = _random_case(70 + seed, fold=True)
+    orc = oracle.Oracle(p)
+    f = p.fixed_axes.astype(np.uint8)
+    fixed = (f[:, 0] | (f[:, 1] << 1) | (f[:, 2] << 2)).astype(np.uint8)
+    rng = np.random.default_rng(seed)
+    for i in range(p.sol_src.shape[0]):
+        s0, t0 = p.sol_src[i], p.sol_tgt[i]
+        noise = rng.normal(size=(16, 64, 3)).astype(np.float32)
+        s, t, moved, sev = orc.repair(s0, t0, noise, max_points=16, fixed=fixed)
+        np.testing.assert_array_equal(s[p.fixed_axes], s0[p.fixed_axes])
+        np.testing.assert_array_equal(t[p.fixed_axes], t0[p.fixed_axes])
+        assert sev <= orc.eval(s0, t0)["severity"] + 1e-15
