@@ -836,7 +836,8 @@ def run_gomea(args):
     in its DSATUR parallel groups; each generation clusters the population
     (host), and per group samples one request per (solution, element) from
     its cluster's distribution (device), evaluates them in one batched
-    partial evaluation (device), accepts (host) and commits (device).
+    partial evaluation (device), accepts (host) and commits (device), then
+    repairs the folded candidates and evaluates the repaired ones.
     Wall-clock time with the device synchronised around each generation.
     value = partial evaluations per second."""
     import time
@@ -848,8 +849,9 @@ def run_gomea(args):
     torch.cuda.set_device(0)
     p = synth.make_c1(n_sol=1)
     n = 128
-    gp = morea.Problem(p, max_solutions=n, max_requests=gomea.max_requests(p, n), max_changed=2)
-    run = gomea.Gomea(gp, p, n, gomea.GomeaConfig(), seed=1)
+    cfg = gomea.GomeaConfig()
+    gp = morea.Problem(p, max_solutions=n, max_requests=gomea.max_requests(p, n), max_changed=gomea.max_changed(cfg))
+    run = gomea.Gomea(gp, p, n, cfg, seed=1)
     ref = 1.1 * run.obj.max(axis=0)
     hv0 = run.hypervolume(ref)
     for _ in range(max(3, args.warmup)):
@@ -857,6 +859,7 @@ def run_gomea(args):
     torch.cuda.synchronize()
     clocks = ClockSampler(0)
     ms, reqs, accs = [], 0, 0
+    calls0 = run.repair_calls
     for _ in range(args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -876,10 +879,12 @@ def run_gomea(args):
                                f"{len(run.groups)} parallel groups of {len(run.el_host)} edge elements; "
                                f"one step = one generation (wall clock, host work included)"},
         "requests_per_generation": reqs / args.steps, "accepted_per_generation": accs / args.steps,
+        "repaired_candidates": run.repaired, "repaired_accepted": run.repaired_accepted,
         "hv_start": hv0, "hv_end": run.hypervolume(ref), "archive": int(len(run.archive.pts)),
         # per group: sampling (2 kernels), partial evaluation (entries, entry work, image pass, guidance,
-        # finalize), commit, slot objectives
-        "gpu_launches": 9 * len(run.groups) * args.steps, "clocks": ck,
+        # finalize), commit, slot objectives; per repair: repair, fold check, partial evaluation (5),
+        # commit, slot objectives
+        "gpu_launches": 9 * len(run.groups) * args.steps + 9 * (run.repair_calls - calls0), "clocks": ck,
     }
     print(json.dumps(line), flush=True)
     gp.close()

@@ -321,13 +321,17 @@ morea_status morea_mlp_info(const morea_mlp *n, int64_t *n_params, int32_t *padd
  * distance to the plane of a face opposite it in its star (at least
  * 2^-k voxel); the trial with the largest decrease of the star's fold
  * severity is kept (lowest index on ties), and the first vertex without a
- * decreasing trial ends that solution's repair.  moved: device [n_sol]
- * number of vertices moved; severity: device [n_sol] fold severity of both
- * meshes afterwards (as morea_check_folds).  The problem's slots and caches
- * are not touched: evaluate the repaired solutions afterwards.
+ * decreasing trial ends that solution's repair.  fixed: device [V] uint8
+ * or NULL; bit a set: axis a of that vertex lies on a face of the image box
+ * and keeps its value in every trial.  moved: device [n_sol] number of
+ * vertices moved; severity: device [n_sol] fold severity of both meshes
+ * afterwards (as morea_check_folds; a degenerate tet is folded but adds no
+ * severity, so check the fold flags, not severity 0).  The problem's slots
+ * and caches are not touched: evaluate the repaired solutions afterwards.
  * MOREA_EINVAL: null pointers, n_sol < 1, max_points < 1, scale not > 0. */
 morea_status morea_repair_folds(morea_problem *p, int32_t n_sol, float *src, float *tgt, const float *noise,
-                                int32_t max_points, float scale, int32_t *moved, double *severity, void *stream);
+                                int32_t max_points, float scale, const uint8_t *fixed, int32_t *moved,
+                                double *severity, void *stream);
 
 /* Objectives of committed slots (a9 from the slots' running totals, which
  * morea_eval_full and morea_commit_partial keep up to date): obj device

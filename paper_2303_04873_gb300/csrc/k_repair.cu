@@ -12,7 +12,8 @@
 // and re-tests, after every move, which of the remaining tets of the chunk
 // are folded.  Scale and trial positions are computed in FP64 with
 // explicitly rounded operations, so they equal the plain definition bit for
-// bit; orientations are exact.
+// bit; orientations are exact.  A coordinate whose axis is fixed for its
+// point (on a face of the image box) keeps its value in every trial.
 #include "morea_device.cuh"
 
 namespace morea {
@@ -75,7 +76,8 @@ __global__ void __launch_bounds__(kRepairWarps * 32) k_repair(const DevProblem *
                                                               const int *__restrict__ v2t_idx, int n_sol,
                                                               float *src, float *tgt,
                                                               const float *__restrict__ noise, int max_points,
-                                                              double scale, int *moved_out, double *sev_out)
+                                                              double scale, const uint8_t *__restrict__ fixed,
+                                                              int *moved_out, double *sev_out)
 {
     extern __shared__ unsigned done_all[];
     const DevProblem &P = *dp;
@@ -128,6 +130,7 @@ __global__ void __launch_bounds__(kRepairWarps * 32) k_repair(const DevProblem *
                     if (!(sigma >= floor_s)) sigma = floor_s;
                     // two trials per lane
                     const float x0 = X[3 * (size_t)v], x1 = X[3 * (size_t)v + 1], x2 = X[3 * (size_t)v + 2];
+                    const unsigned fx = fixed ? fixed[v] : 0u;      // axes on a face of the box stay
                     long long best_gain = 0;
                     int best_k = kTrials;
                     float bq[3] = {0.0f, 0.0f, 0.0f};
@@ -136,9 +139,9 @@ __global__ void __launch_bounds__(kRepairWarps * 32) k_repair(const DevProblem *
                         const int k = lane + 32 * h;
                         const float *z = noise + (((size_t)sol * max_points + visits) * kTrials + k) * 3;
                         float q[3];
-                        q[0] = __double2float_rn(__dadd_rn((double)x0, __dmul_rn(sigma, (double)z[0])));
-                        q[1] = __double2float_rn(__dadd_rn((double)x1, __dmul_rn(sigma, (double)z[1])));
-                        q[2] = __double2float_rn(__dadd_rn((double)x2, __dmul_rn(sigma, (double)z[2])));
+                        q[0] = (fx & 1u) ? x0 : __double2float_rn(__dadd_rn((double)x0, __dmul_rn(sigma, (double)z[0])));
+                        q[1] = (fx & 2u) ? x1 : __double2float_rn(__dadd_rn((double)x1, __dmul_rn(sigma, (double)z[1])));
+                        q[2] = (fx & 4u) ? x2 : __double2float_rn(__dadd_rn((double)x2, __dmul_rn(sigma, (double)z[2])));
                         const int4 qs = snap3(q, P);
                         unsigned long long after = 0;
                         for (int s = s0; s < s1; ++s) after += folded_volume(P, X, v2t_idx[s], v, qs);
@@ -202,6 +205,7 @@ int repair_warps() { return kRepairWarps; }
 
 cudaError_t launch_repair(const DevProblem *dp, const DevProblem &hp, const int *v2t_off, const int *v2t_idx,
                           int n_sol, float *src, float *tgt, const float *noise, int max_points, double scale,
+                          const uint8_t *fixed,
                           int *moved, double *severity, cudaStream_t st)
 {
     const size_t smem = (size_t)kRepairWarps * ((hp.n_points + 31) / 32) * sizeof(unsigned);
@@ -211,7 +215,7 @@ cudaError_t launch_repair(const DevProblem *dp, const DevProblem &hp, const int 
     }
     const int blocks = (n_sol + kRepairWarps - 1) / kRepairWarps;
     k_repair<<<blocks, kRepairWarps * 32, smem, st>>>(dp, v2t_off, v2t_idx, n_sol, src, tgt, noise, max_points,
-                                                      scale, moved, severity);
+                                                      scale, fixed, moved, severity);
     return cudaGetLastError();
 }
 

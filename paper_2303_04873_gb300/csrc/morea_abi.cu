@@ -572,7 +572,8 @@ morea_status morea_init_noise(morea_problem *p, int32_t n_sol, float *src, float
 }
 
 morea_status morea_repair_folds(morea_problem *p, int32_t n_sol, float *src, float *tgt, const float *noise,
-                                int32_t max_points, float scale, int32_t *moved, double *severity, void *stream)
+                                int32_t max_points, float scale, const uint8_t *fixed, int32_t *moved,
+                                double *severity, void *stream)
 {
     if (!p || n_sol < 1 || !src || !tgt || !noise || !moved || !severity || max_points < 1 || !(scale > 0.0f) ||
         std::isinf(scale))
@@ -580,7 +581,7 @@ morea_status morea_repair_folds(morea_problem *p, int32_t n_sol, float *src, flo
     if ((size_t)4 * ((p->V + 31) / 32) * sizeof(unsigned) > 200 * 1024) return MOREA_EINVAL;
     DeviceGuard g(p->device);
     return from_cuda(launch_repair(p->dp, p->hp, p->v2t_off, p->v2t_idx, n_sol, src, tgt, noise, max_points,
-                                   (double)scale, moved, severity, (cudaStream_t)stream));
+                                   (double)scale, fixed, moved, severity, (cudaStream_t)stream));
 }
 
 morea_status morea_check_folds(morea_problem *p, int32_t n_sol, const float *src_pts, const float *tgt_pts,

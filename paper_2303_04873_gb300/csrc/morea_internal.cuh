@@ -180,7 +180,7 @@ cudaError_t launch_dvf(const DevProblem *dp, const DevProblem &hp, const float *
                        unsigned long long *counts, uint8_t *warped, cudaStream_t st);
 // Repair of folded solutions (k_repair.cu), one warp per solution.
 cudaError_t launch_repair(const DevProblem *dp, const DevProblem &hp, const int *v2t_off, const int *v2t_idx,
-                          int n_sol, float *src, float *tgt, const float *noise, int max_points, double scale,
+                          int n_sol, float *src, float *tgt, const float *noise, int max_points, double scale, const uint8_t *fixed,
                           int *moved, double *severity, cudaStream_t st);
 cudaError_t launch_raster(const DevProblem *probs, const DevProblem &hp, const WorkEntry *entries,
                           const RasterSetup *setup, RasterOut *rout, int2 *bandrows, const int *n_entries_dev,

@@ -14,14 +14,21 @@ A generation:
      adaptive steering its f_guidance must also stay within the window
      (Sec. 4.3.2); accepted requests are committed (device) and the
      solutions' objectives re-read from the committed totals (device);
-  4. the archive takes the new solutions; the distribution multiplier of a
+  4. with repair on (the paper's configuration), after each group's commit
+     every solution's first folded candidate of the group is repaired
+     (Sec. 4.3.1; reading R20): rebuilt on the solution as committed,
+     repaired with ``Problem.repair_folds`` (one call per group), and, if
+     the repair (which keeps the fixed axes) leaves it unfolded,
+     re-evaluated as a partial request over every point that differs from
+     the solution and accepted by the same rule;
+  5. the archive takes the new solutions; the distribution multiplier of a
      cluster grows by 10 % after a generation with an accepted request of
      that cluster and shrinks by 10 % otherwise, within [0.1, 10]
      (reading R20); from the steering generation on the archive keeps only
      f_guidance in [s_G, factor s_G] (reading R21).
 
 The initial population comes from ``Problem.init_noise`` (Sec. 4.2.2).
-Folded candidates are discarded (Sec. 4.3.1: the default without repair).
+Without repair, folded candidates are discarded (Sec. 4.3.1).
 """
 
 from __future__ import annotations
@@ -49,11 +56,20 @@ class GomeaConfig:
     init_rounds: int = 50
     init_sigma: tuple = (8.0, 24.0)
     init_strength: tuple = (0.02, 0.15)
+    repair: bool = True              # the paper's runs repair folded candidates
+    repair_points: int = 16          # repair visits per candidate
 
 
 def fixed_bits(fixed_axes: np.ndarray) -> np.ndarray:
     f = np.asarray(fixed_axes, bool).astype(np.uint8)
     return (f[:, 0] | (f[:, 1] << 1) | (f[:, 2] << 2)).astype(np.uint8)
+
+
+def max_changed(cfg: Optional[GomeaConfig] = None) -> int:
+    """The changed-point capacity a Problem needs for Gomea: the two points of
+    an element, plus one per repair visit."""
+    cfg = cfg or GomeaConfig()
+    return 2 + (cfg.repair_points if cfg.repair else 0)
 
 
 def max_requests(prob, n_pop: int) -> int:
@@ -65,12 +81,14 @@ def max_requests(prob, n_pop: int) -> int:
 
 class Gomea:
     """``gp`` must hold at least n_pop slots, max_requests(prob, n_pop)
-    requests and 2 changed points per request."""
+    requests and max_changed(cfg) changed points per request."""
 
     def __init__(self, gp: "morea.Problem", prob, n_pop: int, cfg: Optional[GomeaConfig] = None, seed: int = 0,
                  start_src: Optional[np.ndarray] = None, start_tgt: Optional[np.ndarray] = None):
         self.gp, self.cfg = gp, cfg or GomeaConfig()
         self.rng = np.random.default_rng(seed)
+        self.dev_rng = torch.Generator(device="cuda")     # the repair's trial draws
+        self.dev_rng.manual_seed(int(seed))
         self.dev = torch.device("cuda")
         self.n, self.V = int(n_pop), prob.n_points
         el, grp = morea.parallel_groups(prob.n_points, prob.tets)
@@ -107,6 +125,9 @@ class Gomea:
         self.generation_index = 0
         self.requests = 0
         self.accepted = 0
+        self.repair_calls = 0            # groups whose folded candidates went through the repair
+        self.repaired = 0                # repaired candidates re-evaluated
+        self.repaired_accepted = 0
         biggest = max(len(g) for g in self.groups)
         self.work = torch.empty((morea.sample_elements_workspace(self.cfg.clusters, biggest),), dtype=torch.uint8,
                                 device=self.dev)
@@ -128,6 +149,66 @@ class Gomea:
         for s in range(0, len(o), chunk):
             out[s:s + chunk] = ~np.any(np.all(a[None, :, :] <= o[s:s + chunk, None, :], axis=2), axis=1)
         return out
+
+    def _refresh(self, changed: np.ndarray):
+        """Re-read the committed objectives of the changed solutions and offer
+        them to the archive."""
+        if len(changed) == 0:
+            return
+        obj, _, _ = self.gp.slot_objectives(self.n)
+        obj = obj.cpu().numpy()
+        for i in changed:
+            self.obj[i] = obj[i]
+            self.archive.add(self.obj[i])
+
+    def _accept(self, o: np.ndarray, f: np.ndarray, sol: np.ndarray, hi: float) -> np.ndarray:
+        ok = ~f & np.all(np.isfinite(o), axis=1) & (o[:, 2] <= hi)
+        par = self.obj[sol]
+        better = np.all(o <= par, axis=1) & np.any(o < par, axis=1)
+        return ok & (better | self._archive_accepts(o))
+
+    def _repair(self, sols: np.ndarray, ab: torch.Tensor, cs2: torch.Tensor, ct2: torch.Tensor, hi: float):
+        """Repair one folded candidate per solution ``sols`` (element points ab
+        [k][2], their coordinates cs2 / ct2 [k][2][3]), then evaluate, accept
+        and commit the repaired candidates.  Returns the solutions changed
+        and the numbers re-evaluated and accepted."""
+        c = self.cfg
+        k = len(sols)
+        sol_d = torch.as_tensor(sols).to(self.dev).long()
+        Cs, Ct = self.S[sol_d].clone(), self.T[sol_d].clone()
+        ar = torch.arange(k, device=self.dev)
+        for j in range(2):
+            Cs[ar, ab[:, j]] = cs2[:, j]
+            Ct[ar, ab[:, j]] = ct2[:, j]
+        self.repair_calls += 1
+        noise = torch.randn((k, c.repair_points, 64, 3), generator=self.dev_rng, device=self.dev)
+        self.gp.repair_folds(Cs, Ct, noise, c.repair_points, fixed=self.fixed)
+        folded, _ = self.gp.check_folds(Cs, Ct)          # a degenerate tet is folded without severity
+        diff = ((Cs != self.S[sol_d]) | (Ct != self.T[sol_d])).any(dim=2)
+        n_diff = diff.sum(dim=1)
+        good = (folded == 0) & (n_diff > 0) & (n_diff <= self.gp.max_changed)
+        keep = np.nonzero(good.cpu().numpy())[0]
+        if len(keep) == 0:
+            return np.zeros(0, np.int64), 0, 0
+        keep_d = torch.as_tensor(keep).to(self.dev)
+        sub = diff[keep_d]
+        qi, pi = torch.nonzero(sub, as_tuple=True)           # (candidate, point), candidate-major
+        counts = sub.sum(dim=1).cpu().numpy()
+        off = np.zeros(len(keep) + 1, np.int32)
+        off[1:] = np.cumsum(counts)
+        own = keep_d[qi]
+        cs, ct = Cs[own, pi].contiguous(), Ct[own, pi].contiguous()
+        slots = sol_d[keep_d].int()
+        o, f, _ = self.gp.eval_partial(slots, torch.as_tensor(off).to(self.dev), pi.int().contiguous(), cs, ct)
+        o = o.cpu().numpy()
+        f = f.cpu().numpy().astype(bool)
+        acc = self._accept(o, f, sols[keep], hi).astype(np.uint8)
+        self.gp.commit_partial(torch.as_tensor(acc).to(self.dev))
+        if acc.any():
+            sel = torch.as_tensor(np.repeat(acc, counts).astype(bool)).to(self.dev)
+            self.S[sol_d[own[sel]], pi[sel]] = cs[sel]
+            self.T[sol_d[own[sel]], pi[sel]] = ct[sel]
+        return sols[keep][acc.astype(bool)], len(keep), int(acc.sum())
 
     def step(self) -> dict:
         """One generation; returns its counts."""
@@ -154,11 +235,9 @@ class Gomea:
             o = o.cpu().numpy()
             f = f.cpu().numpy().astype(bool)
             hi = self.window_hi() if steer else np.inf
-            ok = ~f & np.all(np.isfinite(o), axis=1) & (o[:, 2] <= hi)
-            par = self.obj[req_sol]
-            better = np.all(o <= par, axis=1) & np.any(o < par, axis=1)
-            acc = (ok & (better | self._archive_accepts(o))).astype(np.uint8)
+            acc = self._accept(o, f, req_sol, hi).astype(np.uint8)
             self.gp.commit_partial(torch.as_tensor(acc).to(self.dev))
+            changed = np.unique(req_sol[acc.astype(bool)])
             if acc.any():
                 rows = torch.as_tensor(np.nonzero(acc)[0]).to(self.dev)
                 sol = d[0][rows].long()
@@ -166,15 +245,24 @@ class Gomea:
                 for j in range(2):
                     self.S[sol, ab[:, j]] = new_s.view(n_req, 2, 3)[rows, j]
                     self.T[sol, ab[:, j]] = new_t.view(n_req, 2, 3)[rows, j]
-                changed = np.unique(req_sol[acc.astype(bool)])
-                obj, folded, _ = self.gp.slot_objectives(self.n)
-                obj = obj.cpu().numpy()
-                for i in changed:
-                    self.obj[i] = obj[i]
-                    self.archive.add(self.obj[i])
                 hit[np.unique(req_cl[acc.astype(bool)])] = True
+            n_acc = int(acc.sum())
+            self._refresh(changed)
+            fr = np.nonzero(f & np.all(np.isfinite(o), axis=1))[0]
+            if c.repair and len(fr):
+                fs, first = np.unique(req_sol[fr], return_index=True)      # each solution's first folded one
+                rows_d = torch.as_tensor(fr[first]).to(self.dev).long()
+                rsol, n_rep, n_racc = self._repair(fs, gel[d[2][rows_d].long()].long(),
+                                                   new_s.view(n_req, 2, 3)[rows_d], new_t.view(n_req, 2, 3)[rows_d],
+                                                   self.window_hi() if steer else np.inf)
+                self._refresh(rsol)
+                if n_racc:
+                    hit[np.unique(pop_cluster[rsol])] = True
+                self.repaired += n_rep
+                self.repaired_accepted += n_racc
+                n_acc += n_racc
             n_req_total += n_req
-            n_acc_total += int(acc.sum())
+            n_acc_total += n_acc
         self.cmult = np.where(hit, np.minimum(self.cmult * 1.1, 10.0), np.maximum(self.cmult * 0.9, 0.1))
         self.generation_index += 1
         if self.steering() and len(self.archive.pts):
@@ -183,7 +271,8 @@ class Gomea:
             self.archive.pts = pts[pts[:, 2] <= c.steer_factor * s_g]
         self.requests += n_req_total
         self.accepted += n_acc_total
-        return {"requests": n_req_total, "accepted": n_acc_total}
+        return {"requests": n_req_total, "accepted": n_acc_total, "repaired": self.repaired,
+                "repaired_accepted": self.repaired_accepted}
 
     def hypervolume(self, ref) -> float:
         return hv3d(self.archive.pts, ref)

@@ -97,7 +97,7 @@ def lib():
     L.morea_eval_partial.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, u8p, vp, u8p, vp]
     L.morea_commit_partial.argtypes = [vp, i32, u8p, vp]
     L.morea_check_folds.argtypes = [vp, i32, vp, vp, u8p, vp, vp]
-    L.morea_repair_folds.argtypes = [vp, i32, vp, vp, vp, i32, ctypes.c_float, vp, vp, vp]
+    L.morea_repair_folds.argtypes = [vp, i32, vp, vp, vp, i32, ctypes.c_float, vp, vp, vp, vp]
     L.morea_displacement.argtypes = [vp, vp, vp, i32, vp, vp, vp, i32, vp, vp]
     L.morea_parallel_groups.argtypes = [i32, i32, vp, i32, vp, vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
     L.morea_warp_labels.argtypes = [vp, vp, vp, i32, vp, vp, vp]
@@ -392,9 +392,10 @@ class Problem:
                                             _stream(stream)), "morea_commit_partial")
 
     def repair_folds(self, src: torch.Tensor, tgt: torch.Tensor, noise: torch.Tensor, max_points: int,
-                     scale: float = 1.0, stream=None):
-        """Repair (Sec. 4.3.1) of src/tgt [n][V][3] in place; noise [n][max_points][64][3] N(0,1).
-        Returns (moved [n] int32, severity [n] f64) on the device."""
+                     scale: float = 1.0, fixed: Optional[torch.Tensor] = None, stream=None):
+        """Repair (Sec. 4.3.1) of src/tgt [n][V][3] in place; noise [n][max_points][64][3] N(0,1);
+        fixed [V] uint8 axis bits of coordinates that stay.  Returns (moved [n] int32,
+        severity [n] f64) on the device."""
         n = int(src.shape[0])
         V = self.n_points
         moved = torch.empty((n,), dtype=torch.int32, device=src.device)
@@ -402,6 +403,7 @@ class Problem:
         _check(self._L.morea_repair_folds(
             self._h, n, _dev(src, torch.float32, (n, V, 3), "src"), _dev(tgt, torch.float32, (n, V, 3), "tgt"),
             _dev(noise, torch.float32, (n, int(max_points), 64, 3), "noise"), int(max_points), float(scale),
+            _dev(fixed, torch.uint8, (V,), "fixed"),
             _dev(moved, torch.int32, (n,), "moved"), _dev(sev, torch.float64, (n,), "severity"),
             _stream(stream)), "morea_repair_folds")
         return moved, sev

@@ -123,7 +123,7 @@ def test_generations_keep_their_invariants(mo):
     n = 16
     cfg = gomea.GomeaConfig(clusters=4, steer_at=1000, init_kernels=4, init_rounds=20, init_sigma=(3.0, 9.0),
                             init_strength=(0.05, 0.2))
-    gp = mo.Problem(p, max_solutions=n, max_requests=gomea.max_requests(p, n), max_changed=2)
+    gp = mo.Problem(p, max_solutions=n, max_requests=gomea.max_requests(p, n), max_changed=gomea.max_changed(cfg))
     run = gomea.Gomea(gp, p, n, cfg, seed=4)
     ref = 1.1 * run.obj.max(axis=0)
     hv = [run.hypervolume(ref)]
@@ -148,9 +148,37 @@ def test_adaptive_steering_window(mo):
     n = 16
     cfg = gomea.GomeaConfig(clusters=4, steer_at=2, init_kernels=4, init_rounds=20, init_sigma=(3.0, 9.0),
                             init_strength=(0.05, 0.2))
-    gp = mo.Problem(p, max_solutions=n, max_requests=gomea.max_requests(p, n), max_changed=2)
+    gp = mo.Problem(p, max_solutions=n, max_requests=gomea.max_requests(p, n), max_changed=gomea.max_changed(cfg))
     run = gomea.Gomea(gp, p, n, cfg, seed=5)
     for _ in range(4):
         run.step()
     g = run.archive.pts[:, 2]
     assert np.all(g <= 1.5 * g.min() + 1e-15)
+
+
+def test_folded_candidates_are_repaired(mo):
+    """A large distribution multiplier makes many candidates fold, and the
+    repair path runs every generation.  Acceptance is widened to every
+    unfolded candidate (the rule itself is tested above), so repaired
+    candidates are committed too: the committed objectives must still equal
+    a fresh evaluation, with every boundary axis in place."""
+    from paper_2303_04873_gb300 import gomea
+    p = synth.make_c0(n_sol=1)
+    n = 16
+    cfg = gomea.GomeaConfig(clusters=4, steer_at=1000, init_kernels=4, init_rounds=20, init_sigma=(3.0, 9.0),
+                            init_strength=(0.05, 0.2), cmult0=6.0, repair_points=8)
+    gp = mo.Problem(p, max_solutions=n, max_requests=gomea.max_requests(p, n), max_changed=gomea.max_changed(cfg))
+    run = gomea.Gomea(gp, p, n, cfg, seed=6)
+    run._accept = lambda o, f, sol, hi: ~f & np.all(np.isfinite(o), axis=1)
+    for _ in range(3):
+        run.step()
+    assert run.repaired > 0 and run.repaired_accepted > 0
+    fresh = mo.Problem(p, max_solutions=n)
+    o, f, _ = fresh.eval_full(run.S, run.T)
+    np.testing.assert_allclose(o.cpu().numpy(), run.obj, rtol=1e-9)
+    assert not f.cpu().numpy().any()
+    fx = p.fixed_axes
+    for X in (run.S.cpu().numpy(), run.T.cpu().numpy()):
+        np.testing.assert_array_equal(X[:, fx], np.broadcast_to(p.ref_points[fx], (n,) + p.ref_points[fx].shape))
+    _pareto_ok(run.archive.pts)
+    assert gp.device_status() == 0

@@ -23,14 +23,15 @@ def mo():
     return morea
 
 
-def run_both(mo, p, src, tgt, max_points, scale, seed):
+def run_both(mo, p, src, tgt, max_points, scale, seed, fixed=None):
     n = src.shape[0]
     rng = np.random.default_rng(seed)
     noise = rng.normal(size=(n, max_points, 64, 3)).astype(np.float32)
     gp = mo.Problem(p, max_solutions=n)
     S = torch.as_tensor(np.ascontiguousarray(src, np.float32)).cuda()
     T = torch.as_tensor(np.ascontiguousarray(tgt, np.float32)).cuda()
-    moved, sev = gp.repair_folds(S, T, torch.as_tensor(noise).cuda(), max_points, scale)
+    fx = None if fixed is None else torch.as_tensor(fixed).cuda()
+    moved, sev = gp.repair_folds(S, T, torch.as_tensor(noise).cuda(), max_points, scale, fixed=fx)
     torch.cuda.synchronize()
     orc = oracle.Oracle(p, subvoxel_bits=gp.subvoxel_bits)
     return S.cpu().numpy(), T.cpu().numpy(), moved.cpu().numpy(), sev.cpu().numpy(), orc, noise
@@ -48,6 +49,21 @@ def test_repair_matches_oracle_on_random_folded_meshes(mo, seed, scale):
         assert sev[i] == sv, i
         np.testing.assert_array_equal(S[i], s)
         np.testing.assert_array_equal(T[i], t)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_repair_with_fixed_boundary_axes(mo, seed):
+    p = _random_case(70 + seed, fold=True)
+    f = p.fixed_axes.astype(np.uint8)
+    fixed = (f[:, 0] | (f[:, 1] << 1) | (f[:, 2] << 2)).astype(np.uint8)
+    mp = 12
+    S, T, moved, sev, orc, noise = run_both(mo, p, p.sol_src, p.sol_tgt, mp, 1.0, seed, fixed=fixed)
+    for i in range(p.sol_src.shape[0]):
+        s, t, m, sv = orc.repair(p.sol_src[i], p.sol_tgt[i], noise[i], mp, 1.0, fixed=fixed)
+        assert moved[i] == m and sev[i] == sv, i
+        np.testing.assert_array_equal(S[i], s)
+        np.testing.assert_array_equal(T[i], t)
+        np.testing.assert_array_equal(S[i][p.fixed_axes], p.sol_src[i][p.fixed_axes])
 
 
 def test_repair_on_the_full_size_mesh(mo):
