@@ -89,12 +89,10 @@ def workload(seed_offset=0, name="c1", estimator="voxels"):
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the timed
 # image pass (k_raster + k_guidance) per launch, averaged over one step's 21
-# launches, from an ncu capture of `bench.py --workload <w> --steps 1`.  Valid
-# only for the kernel source it was taken on (SHA-256 of k_raster.cu); after
-# any change to that file the bench reports null until it is re-measured.
-# DRAM traffic of the image pass from one ncu capture (see profiles/), valid
-# only while the image kernels and the work-list builder are unchanged: the
-# digest covers both source files.
+# launches, from an ncu capture of `bench.py --workload <w> --steps 1` (see
+# profiles/).  Valid only while the image kernels and the work-list builder
+# are unchanged: the digest covers both source files, and after any change
+# the bench reports null until the traffic is re-measured.
 TRAFFIC_SOURCES = ("k_raster.cu", "k_tet.cu")
 MEASURED_TRAFFIC = {
     "c1": {"bytes_per_launch": 120586453,
