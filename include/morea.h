@@ -381,7 +381,8 @@ size_t morea_sample_elements_workspace(int32_t n_clusters, int32_t n_elements);
  *                element of each new partial solution
  *   z            device [n_req][12] standard normal draws (the caller's)
  *   work         device workspace of morea_sample_elements_workspace()
- *                bytes (caller-owned, not preserved between calls)
+ *                bytes, 16-byte aligned (caller-owned, not preserved
+ *                between calls)
  *   new_src, new_tgt  device [n_req][2][3]: the new coordinates of points a
  *                and b of each request: the candidate rows of a
  *                morea_eval_partial request whose changed points are (a, b)
@@ -390,7 +391,7 @@ size_t morea_sample_elements_workspace(int32_t n_clusters, int32_t n_elements);
  * Sigma + 1e-6 I over the free variables, all FP64; a request draws
  * mu + cmult L z, rounded to FP32.  An index out of range yields NaN rows.
  * Stream-ordered, no allocation.  MOREA_EINVAL: null pointers, counts out of
- * range, misaligned elements, work_bytes too small. */
+ * range, misaligned elements or work, work_bytes too small. */
 morea_status morea_sample_elements(morea_problem *p, int32_t n_pop, const float *src, const float *tgt,
                                    int32_t n_clusters, int32_t cluster_size, const int32_t *members,
                                    int32_t n_elements, const int32_t *elements, const uint8_t *fixed,
@@ -480,8 +481,9 @@ size_t morea_surface_distance_workspace(int32_t nx, int32_t ny, int32_t nz);
  * `label` in two label images (the evaluation metrics of Sec. 5).
  *   a, b     device [nz][ny][nx] uint8 label images; 1 <= nx, ny, nz <= 1024
  *   label    0..255; a mask is the set of voxels equal to it
- *   work     device workspace of morea_surface_distance_workspace() bytes
- *            (caller-owned; its contents need not be preserved between calls)
+ *   work     device workspace of morea_surface_distance_workspace() bytes,
+ *            256-byte aligned (caller-owned; its contents need not be
+ *            preserved between calls)
  *   out      device double[4]: HD, HD95 (voxel units), |S_a|, |S_b|
  * The surface of a mask is its voxels with a face neighbour outside the
  * mask (beyond the image border counts as outside).  The directed distances
@@ -491,7 +493,8 @@ size_t morea_surface_distance_workspace(int32_t nx, int32_t ny, int32_t nz);
  * the two directed 95th percentiles, each by nearest rank (the
  * ceil(0.95 n)-th smallest).  An empty surface gives NaN for HD and HD95.
  * Stream-ordered, no allocation, no host synchronisation.  MOREA_EINVAL:
- * sizes out of range, null pointers, work_bytes too small. */
+ * sizes out of range, null pointers, work_bytes too small or work not
+ * 256-byte aligned. */
 morea_status morea_surface_distance(int32_t nx, int32_t ny, int32_t nz, const uint8_t *a, const uint8_t *b,
                                     int32_t label, void *work, size_t work_bytes, double *out, void *stream);
 

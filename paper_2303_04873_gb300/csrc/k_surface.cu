@@ -338,7 +338,7 @@ extern "C" morea_status morea_surface_distance(int32_t nx, int32_t ny, int32_t n
 {
     if (!extents_ok(nx, ny, nz) || !a || !b || !work || !out || label < 0 || label > 255) return MOREA_EINVAL;
     const Layout Lo = layout(nx, ny, nz);
-    if (work_bytes < Lo.total) return MOREA_EINVAL;
+    if (work_bytes < Lo.total || (reinterpret_cast<uintptr_t>(work) & 255) != 0) return MOREA_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     char *w = static_cast<char *>(work);
     uint8_t *surf = reinterpret_cast<uint8_t *>(w + Lo.surf);

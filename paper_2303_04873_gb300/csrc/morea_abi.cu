@@ -550,7 +550,8 @@ morea_status morea_sample_elements(morea_problem *p, int32_t n_pop, const float 
         !elements || !cmult || n_req < 0 || !work)
         return MOREA_EINVAL;
     if (n_req > 0 && (!req_sol || !req_cluster || !req_element || !z || !new_src || !new_tgt)) return MOREA_EINVAL;
-    if ((reinterpret_cast<uintptr_t>(elements) & 7) != 0) return MOREA_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(elements) & 7) != 0 || (reinterpret_cast<uintptr_t>(work) & 15) != 0)
+        return MOREA_EINVAL;
     if (work_bytes < sample_elements_bytes(n_clusters, n_elements)) return MOREA_EINVAL;
     DeviceGuard g(p->device);
     return from_cuda(launch_sample_elements(p->V, n_pop, src, tgt, n_clusters, cluster_size, members, n_elements,

@@ -170,4 +170,7 @@ def test_surface_distance_arguments_checked_on_host(mo):
     args = list(ok)
     args[7] = ok[7] - 1                # workspace one byte short
     assert L.morea_surface_distance(*args) == mo.EINVAL
+    args = list(ok)
+    args[6] = ctypes.c_void_p(256 + 16)   # workspace not 256-byte aligned
+    assert L.morea_surface_distance(*args) == mo.EINVAL
     assert L.morea_warp_labels(None, fake, fake, 0, fake, fake, None) == mo.EINVAL
