@@ -182,3 +182,28 @@ def test_folded_candidates_are_repaired(mo):
         np.testing.assert_array_equal(X[:, fx], np.broadcast_to(p.ref_points[fx], (n,) + p.ref_points[fx].shape))
     _pareto_ok(run.archive.pts)
     assert gp.device_status() == 0
+
+
+def test_generations_on_the_full_size_problem(mo):
+    """Two generations on the 128x128x96 problem (population 32, the paper's
+    10 clusters, repair on): committed objectives equal a fresh evaluation
+    of the device coordinates, nothing is folded, boundary axes stay."""
+    from paper_2303_04873_gb300 import gomea
+    p = synth.make_c1(n_sol=1)
+    n = 32
+    cfg = gomea.GomeaConfig()
+    gp = mo.Problem(p, max_solutions=n, max_requests=gomea.max_requests(p, n), max_changed=gomea.max_changed(cfg))
+    run = gomea.Gomea(gp, p, n, cfg, seed=9)
+    for _ in range(2):
+        st = run.step()
+        assert st["requests"] == n * len(run.el_host)
+    assert run.accepted > 0
+    fresh = mo.Problem(p, max_solutions=n)
+    o, f, _ = fresh.eval_full(run.S, run.T)
+    np.testing.assert_allclose(o.cpu().numpy(), run.obj, rtol=1e-9)
+    assert not f.cpu().numpy().any()
+    fx = p.fixed_axes
+    for X in (run.S.cpu().numpy(), run.T.cpu().numpy()):
+        np.testing.assert_array_equal(X[:, fx], np.broadcast_to(p.ref_points[fx], (n,) + p.ref_points[fx].shape))
+    _pareto_ok(run.archive.pts)
+    assert gp.device_status() == 0
