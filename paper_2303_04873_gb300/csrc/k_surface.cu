@@ -25,7 +25,7 @@
 //   k_select     nearest-rank 95th percentile of each direction from its
 //                histogram (one block, chunked block scan), and the outputs
 //
-// Workspace: surface bits [N] u8, three int32 fields [N], two histograms of
+// Workspace: surface bits [N] u8, four int32 fields [N], two histograms of
 // (nx-1)^2 + (ny-1)^2 + (nz-1)^2 + 1 bins, counters.  Nothing is allocated.
 #include <math.h>
 #include <stdint.h>
@@ -68,7 +68,7 @@ __device__ __forceinline__ Box read_box(const Counters *c)
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
-    size_t surf, fa, fb, tmp, hist, ctr, total;
+    size_t surf, fa, fb, ta, tb, hist, ctr, total;
     long long n_bins;
 };
 
@@ -80,8 +80,9 @@ Layout layout(int nx, int ny, int nz)
     L.surf = 0;
     L.fa = align256(N);
     L.fb = L.fa + align256(4 * N);
-    L.tmp = L.fb + align256(4 * N);
-    L.hist = L.tmp + align256(4 * N);
+    L.ta = L.fb + align256(4 * N);
+    L.tb = L.ta + align256(4 * N);
+    L.hist = L.tb + align256(4 * N);
     L.ctr = L.hist + align256(8 * (size_t)L.n_bins);
     L.total = L.ctr + align256(sizeof(Counters));
     return L;
@@ -192,10 +193,14 @@ __global__ void k_edt_x(int nx, int ny, int nz, const uint8_t *__restrict__ surf
 // f_out at (i, line position j, o) = min over q of f_in(i, q, o) + (j - q)^2
 // inside the box: line axis la (element stride ls), other axis oa (block
 // row o, stride os), i along x (stride 1).  Block: 32 x-neighbours x
-// kLineThreadsY; blocks outside the box return at once.
+// kLineThreadsY; blocks outside the box return at once.  blockIdx.z picks
+// the surface: both transforms advance in one launch.
 __global__ void k_edt_line(int nx, int la, long long ls, int oa, long long os, const Counters *__restrict__ ctr,
-                           const int *__restrict__ fin, int *__restrict__ fout)
+                           const int *__restrict__ fin0, int *__restrict__ fout0, const int *__restrict__ fin1,
+                           int *__restrict__ fout1)
 {
+    const int *__restrict__ fin = blockIdx.z ? fin1 : fin0;
+    int *__restrict__ fout = blockIdx.z ? fout1 : fout0;
     extern __shared__ int col[];                       // [line extent of the box][32]
     const Box bx = read_box(ctr);
     const int o = blockIdx.y, i0 = blockIdx.x * 32;
@@ -312,15 +317,15 @@ bool extents_ok(int nx, int ny, int nz)
 // L: the image extent along the line axis (the box is at most that long),
 // n_o: along the other axis.
 cudaError_t launch_line(int nx, int la, int L, long long ls, int oa, int n_o, long long os, const Counters *ctr,
-                        const int *fin, int *fout, cudaStream_t st)
+                        const int *fin0, int *fout0, const int *fin1, int *fout1, cudaStream_t st)
 {
     const size_t smem = (size_t)L * 32 * sizeof(int);
     if (smem > 48 * 1024) {
         const cudaError_t e = cudaFuncSetAttribute(k_edt_line, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    const dim3 grid((unsigned)((nx + 31) / 32), (unsigned)n_o);
-    k_edt_line<<<grid, dim3(32, kLineThreadsY), smem, st>>>(nx, la, ls, oa, os, ctr, fin, fout);
+    const dim3 grid((unsigned)((nx + 31) / 32), (unsigned)n_o, 2);
+    k_edt_line<<<grid, dim3(32, kLineThreadsY), smem, st>>>(nx, la, ls, oa, os, ctr, fin0, fout0, fin1, fout1);
     return cudaGetLastError();
 }
 
@@ -344,7 +349,8 @@ extern "C" morea_status morea_surface_distance(int32_t nx, int32_t ny, int32_t n
     uint8_t *surf = reinterpret_cast<uint8_t *>(w + Lo.surf);
     int *fa = reinterpret_cast<int *>(w + Lo.fa);
     int *fb = reinterpret_cast<int *>(w + Lo.fb);
-    int *tmp = reinterpret_cast<int *>(w + Lo.tmp);
+    int *ta = reinterpret_cast<int *>(w + Lo.ta);
+    int *tb = reinterpret_cast<int *>(w + Lo.tb);
     unsigned *hist = reinterpret_cast<unsigned *>(w + Lo.hist);
     Counters *ctr = reinterpret_cast<Counters *>(w + Lo.ctr);
     const long long N = (long long)nx * ny * nz;
@@ -358,13 +364,10 @@ extern "C" morea_status morea_surface_distance(int32_t nx, int32_t ny, int32_t n
     const int row_blocks = (int)std::min<long long>(((long long)ny * nz + 7) / 8, 152LL * 16);
     k_edt_x<<<row_blocks, 256, 0, st>>>(nx, ny, nz, surf, ctr, fa, fb);
     if ((e = cudaGetLastError()) != cudaSuccess) return MOREA_ECUDA;
-    for (int m = 0; m < 2; ++m) {
-        int *f = m == 0 ? fa : fb;
-        // along y: lines (i, ., k), element stride nx, one block row per z-plane
-        if ((e = launch_line(nx, 1, ny, nx, 2, nz, plane, ctr, f, tmp, st)) != cudaSuccess) return MOREA_ECUDA;
-        // along z: lines (i, j, .), element stride nx*ny, one block row per y
-        if ((e = launch_line(nx, 2, nz, plane, 1, ny, nx, ctr, tmp, f, st)) != cudaSuccess) return MOREA_ECUDA;
-    }
+    // along y: lines (i, ., k), element stride nx, one block row per z-plane; both surfaces
+    if ((e = launch_line(nx, 1, ny, nx, 2, nz, plane, ctr, fa, ta, fb, tb, st)) != cudaSuccess) return MOREA_ECUDA;
+    // along z: lines (i, j, .), element stride nx*ny, one block row per y
+    if ((e = launch_line(nx, 2, nz, plane, 1, ny, nx, ctr, ta, fa, tb, fb, st)) != cudaSuccess) return MOREA_ECUDA;
     k_directed<<<blocks, 256, 0, st>>>(N, surf, fa, fb, Lo.n_bins, hist, ctr);
     k_select<<<1, 1024, 0, st>>>(Lo.n_bins, hist, ctr, out);
     return cudaGetLastError() == cudaSuccess ? MOREA_OK : MOREA_ECUDA;

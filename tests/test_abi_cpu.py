@@ -156,7 +156,7 @@ def test_surface_distance_arguments_checked_on_host(mo):
     need = mo.surface_distance_workspace(128, 128, 96)
     N = 128 * 128 * 96
     bins = 127 ** 2 + 127 ** 2 + 95 ** 2 + 1
-    assert need >= N + 12 * N + 8 * bins
+    assert need >= N + 16 * N + 8 * bins
     assert need % 256 == 0
     assert L.morea_surface_distance_workspace(0, 4, 4) == 0
     assert L.morea_surface_distance_workspace(1025, 4, 4) == 0
