@@ -21,9 +21,10 @@
 //                reads shared memory only
 //   k_directed   at every surface voxel of a, the squared distance to b's
 //                surface (b's transform), and vice versa: maximum and a
-//                histogram of squared distances per direction
-//   k_select     nearest-rank 95th percentile of each direction from its
-//                histogram (one block, chunked block scan), and the outputs
+//                histogram of squared distances per direction; the last
+//                block to finish takes the nearest-rank 95th percentile of
+//                each direction from its histogram (chunked block scan) and
+//                writes the outputs
 //
 // Workspace: surface bits [N] u8, four int32 fields [N], two histograms of
 // (nx-1)^2 + (ny-1)^2 + (nz-1)^2 + 1 bins, counters.  Nothing is allocated.
@@ -48,6 +49,7 @@ struct Counters {
     unsigned int max_sq[2];                  // largest directed squared distance a->b, b->a
     unsigned int lo_inv[3];                  // per axis: max of (kMaxExtent - coordinate) over surface voxels
     unsigned int hi_p1[3];                   //           max of (coordinate + 1); zero-initialised: empty box
+    unsigned int done;                       // blocks of k_directed finished
 };
 
 struct Box {
@@ -230,9 +232,73 @@ __global__ void k_edt_line(int nx, int la, long long ls, int oa, long long os, c
     }
 }
 
-__global__ void k_directed(long long N, const uint8_t *__restrict__ surf, const int *__restrict__ fa,
-                           const int *__restrict__ fb, long long n_bins, unsigned *__restrict__ hist, Counters *ctr)
+// Nearest-rank 95th percentile of each direction from its histogram (a
+// chunked block scan), and the outputs.  Run by one whole block; the
+// histograms and counters are read from L2, where the atomics landed.
+__device__ void select_and_write(long long n_bins, const unsigned *hist, const Counters *ctr, double *out)
 {
+    __shared__ unsigned long long warp_tot[32];
+    __shared__ long long found;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5, nt = blockDim.x, nw = nt >> 5;
+    const unsigned long long na = __ldcg(&ctr->n[0]), nb = __ldcg(&ctr->n[1]);
+    long long p95[2] = {0, 0};
+    for (int dir = 0; dir < 2; ++dir) {
+        const unsigned long long n = dir == 0 ? na : nb;
+        const unsigned long long r = (95ull * n + 99ull) / 100ull;   // nearest rank, 1-based
+        const unsigned *h = hist + dir * n_bins;
+        unsigned long long run = 0;
+        if (t == 0) found = -1;
+        __syncthreads();
+        for (long long b0 = 0; b0 < n_bins && n > 0; b0 += nt) {
+            const long long bin = b0 + t;
+            const unsigned long long own = bin < n_bins ? __ldcg(h + bin) : 0ull;
+            unsigned long long c = own;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long u = __shfl_up_sync(FULL, c, o);
+                if (lane >= o) c += u;
+            }
+            if (lane == 31) warp_tot[w] = c;
+            __syncthreads();
+            unsigned long long before = 0, chunk = 0;
+            for (int x = 0; x < nw; ++x) {
+                const unsigned long long v = warp_tot[x];
+                if (x < w) before += v;
+                chunk += v;
+            }
+            const unsigned long long incl = run + before + c;
+            const unsigned long long prev = incl - own;
+            if (bin < n_bins && prev < r && incl >= r) found = bin;   // exactly one bin crosses r
+            __syncthreads();
+            run += chunk;
+            if (found >= 0) break;
+        }
+        p95[dir] = found;
+        __syncthreads();
+    }
+    if (t == 0) {
+        if (na == 0 || nb == 0) {
+            out[0] = NAN;
+            out[1] = NAN;
+        } else {
+            const unsigned m0 = __ldcg(&ctr->max_sq[0]), m1 = __ldcg(&ctr->max_sq[1]);
+            out[0] = sqrt((double)max(m0, m1));
+            out[1] = sqrt((double)max(p95[0], p95[1]));
+        }
+        out[2] = (double)na;
+        out[3] = (double)nb;
+    }
+}
+
+// At every surface voxel of a, the squared distance to b's surface (b's
+// transform), and vice versa: maximum and histogram per direction.  The
+// last block to finish then selects the percentiles and writes the outputs.
+__global__ void __launch_bounds__(256) k_directed(long long N, const uint8_t *__restrict__ surf,
+                                                  const int *__restrict__ fa, const int *__restrict__ fb,
+                                                  long long n_bins, unsigned *__restrict__ hist, Counters *ctr,
+                                                  double *out)
+{
+    __shared__ bool last;
     for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < N;
          v += (long long)gridDim.x * blockDim.x) {
         const unsigned s = surf[v];
@@ -252,60 +318,15 @@ __global__ void k_directed(long long N, const uint8_t *__restrict__ surf, const 
             }
         }
     }
-}
-
-// One block of 1024 threads.
-__global__ void __launch_bounds__(1024) k_select(long long n_bins, const unsigned *__restrict__ hist,
-                                                 const Counters *__restrict__ ctr, double *out)
-{
-    __shared__ unsigned long long warp_tot[32];
-    __shared__ long long found;
-    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    const unsigned long long na = ctr->n[0], nb = ctr->n[1];
-    long long p95[2] = {0, 0};
-    for (int dir = 0; dir < 2; ++dir) {
-        const unsigned long long n = dir == 0 ? na : nb;
-        const unsigned long long r = (95ull * n + 99ull) / 100ull;   // nearest rank, 1-based
-        const unsigned *h = hist + dir * n_bins;
-        unsigned long long run = 0;
-        if (t == 0) found = -1;
-        __syncthreads();
-        for (long long b0 = 0; b0 < n_bins && n > 0; b0 += 1024) {
-            const long long bin = b0 + t;
-            unsigned long long c = bin < n_bins ? h[bin] : 0ull;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned long long u = __shfl_up_sync(FULL, c, o);
-                if (lane >= o) c += u;
-            }
-            if (lane == 31) warp_tot[w] = c;
-            __syncthreads();
-            unsigned long long before = 0, chunk = 0;
-            for (int x = 0; x < 32; ++x) {
-                const unsigned long long v = warp_tot[x];
-                if (x < w) before += v;
-                chunk += v;
-            }
-            const unsigned long long incl = run + before + c;
-            const unsigned long long prev = incl - (bin < n_bins ? h[bin] : 0ull);
-            if (bin < n_bins && prev < r && incl >= r) found = bin;   // exactly one bin crosses r
-            __syncthreads();
-            run += chunk;
-            if (found >= 0) break;
-        }
-        p95[dir] = found;
-        __syncthreads();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&ctr->done, 1u) == gridDim.x - 1;
     }
-    if (t == 0) {
-        if (na == 0 || nb == 0) {
-            out[0] = NAN;
-            out[1] = NAN;
-        } else {
-            out[0] = sqrt((double)max(ctr->max_sq[0], ctr->max_sq[1]));
-            out[1] = sqrt((double)max(p95[0], p95[1]));
-        }
-        out[2] = (double)na;
-        out[3] = (double)nb;
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        select_and_write(n_bins, hist, ctr, out);
     }
 }
 
@@ -368,7 +389,6 @@ extern "C" morea_status morea_surface_distance(int32_t nx, int32_t ny, int32_t n
     if ((e = launch_line(nx, 1, ny, nx, 2, nz, plane, ctr, fa, ta, fb, tb, st)) != cudaSuccess) return MOREA_ECUDA;
     // along z: lines (i, j, .), element stride nx*ny, one block row per y
     if ((e = launch_line(nx, 2, nz, plane, 1, ny, nx, ctr, ta, fa, tb, fb, st)) != cudaSuccess) return MOREA_ECUDA;
-    k_directed<<<blocks, 256, 0, st>>>(N, surf, fa, fb, Lo.n_bins, hist, ctr);
-    k_select<<<1, 1024, 0, st>>>(Lo.n_bins, hist, ctr, out);
+    k_directed<<<blocks, 256, 0, st>>>(N, surf, fa, fb, Lo.n_bins, hist, ctr, out);
     return cudaGetLastError() == cudaSuccess ? MOREA_OK : MOREA_ECUDA;
 }
