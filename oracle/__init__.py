@@ -29,6 +29,7 @@ TET_DTYPE = np.dtype([
     ("e_img", "<f8", (2,)), ("e_guid", "<f8", (2,)),
     ("n_vox", "<i8", (2,)), ("n_gp", "<i8", (2,)),
     ("e_mag", "<f8"), ("sev", "<u8"), ("folded", "<i4"), ("pad", "<i4"),
+    ("amb_n", "<i8", (2,)), ("amb_slack", "<f8", (2,)),
 ])
 
 
@@ -126,7 +127,9 @@ def lib():
         L.orc_repair_sigma.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double]
         L.orc_repair_sigma.restype = ctypes.c_double
         L.orc_dvf.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
-                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                              ctypes.c_void_p]
+        L.orc_set_perturbation.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double]
         L.orc_dvf.restype = ctypes.c_int
         L.orc_gexp.argtypes = [ctypes.c_double]
         L.orc_gexp.restype = ctypes.c_double
@@ -281,23 +284,34 @@ class Oracle:
             lt = np.ascontiguousarray(labels_other, dtype=np.uint8)
             counts = np.zeros((n_labels, 3), np.int64)
         rc = self._L.orc_dvf(self._h, _ptr(s), _ptr(t), int(side), _ptr(out), _ptr(lo), _ptr(lt), int(n_labels),
-                             _ptr(counts), None)
+                             _ptr(counts), None, None)
         if rc != 0:
             raise OracleError("oracle dvf failed")
         return out, counts
 
-    def warp_labels(self, src, tgt, side: int, labels_other):
+    def warp_labels(self, src, tgt, side: int, labels_other, candidates: bool = False):
         """R15/R17: the other image's label at the voxel nearest to T(p) for
         every voxel centre p covered by an unfolded copy of mesh ``side``;
-        255 where no copy covers p."""
+        255 where no copy covers p.  With ``candidates``, also the [nz][ny][nx][8]
+        labels the perturbation report allows per voxel (``set_perturbation``)."""
         s = np.ascontiguousarray(src, dtype=np.float32)
         t = np.ascontiguousarray(tgt, dtype=np.float32)
         lt = np.ascontiguousarray(labels_other, dtype=np.uint8)
         warped = np.zeros((self.nz, self.ny, self.nx), np.uint8)
-        rc = self._L.orc_dvf(self._h, _ptr(s), _ptr(t), int(side), None, None, _ptr(lt), 0, None, _ptr(warped))
+        cand = np.zeros((self.nz, self.ny, self.nx, 8), np.uint8) if candidates else None
+        rc = self._L.orc_dvf(self._h, _ptr(s), _ptr(t), int(side), None, None, _ptr(lt), 0, None, _ptr(warped),
+                             _ptr(cand))
         if rc != 0:
             raise OracleError("oracle warp_labels failed")
-        return warped
+        return (warped, cand) if candidates else warped
+
+    def set_perturbation(self, gamma_pos: float, gamma_val: float):
+        """Turn on (radii > 0) or off the perturbation report: per voxel the
+        decisions of R9 (case of h) and R15 (nearest voxel) that change when
+        the mapped position moves by gamma_pos (|t0| + |M||p - s0| + 1) per
+        axis and the sample by the matching radius plus gamma_val times the
+        largest stored value.  Returned values never change."""
+        self._L.orc_set_perturbation(self._h, float(gamma_pos), float(gamma_val))
 
     def init_noise(self, X, kernels, fixed=None, max_rounds: int = 20):
         """R18: one mesh X [V][3] after the attraction rounds of the kernels

@@ -50,11 +50,13 @@
  *      |T(g_s) - g_t|^2 and |T'(g_t) - g_s|^2 over located points; a point
  *      is located with R3 on its snapped coordinates.
  *   R9 h in the foreground/background mode jumps at b = 0 (from (a-b)^2 to
- *      1), so which case applies is a decision taken by floating point.  The
- *      oracle takes it in the GPU kernel's precision: b is recomputed in FP32
- *      (affine map t0 + M (p - s0) with M = F adj(E) / D rounded to float,
- *      clamped cell, fused multiply-add lerps) and only its comparison with
- *      0 is used; the value (a - b)^2 itself is the FP64 sample.
+ *      1).  The case is decided on the sample b of the stored image values
+ *      at the exact T(p), as Sec. 4.1.2 defines h on the sampled
+ *      intensities: T(p) of a voxel centre is kept as an exact rational, so
+ *      the clamp, the cell and a zero fraction are exact, and b is the
+ *      8-corner sum with each fraction rounded once (FP64).  Where a caller evaluates T(p) and b in lower
+ *      precision the decision can differ close to b = 0; orc_set_perturbation
+ *      turns on a per-voxel report of exactly those voxels (see below).
  *   R13 sampled estimator (App. A.2, the paper's own estimator; estimator =
  *      1).  Per tet copy with orient D > 0: N = floor(rate * vol + 1/2)
  *      points (capped at 2^24), vol = D / (6 2^3k) voxel^3 in FP64, rate the
@@ -90,12 +92,11 @@
  *      dvf(p) = T(p) - p with the FP64 barycentric map; voxels in no copy
  *      are NaN, and a voxel inside several copies (folded or overlapping
  *      meshes only) takes the first copy in tet order.  Label overlap: the
- *      nearest voxel of the other image to T(p) (round half to even,
- *      clamped to the image) gives the pulled-back label, with T(p) taken
- *      in the GPU kernel's FP32 arithmetic because floating point decides
- *      the integer (as R9); per label l the counts of covered voxels with
- *      own label l, with pulled-back label l, and with both.  The warped
- *      label image holds the pulled-back label per voxel, 255 in no copy.
+ *      nearest voxel of the other image to the exact (rational) T(p), round
+ *      half to even, clamped to the image, gives the pulled-back label; per label l
+ *      the counts of covered voxels with own label l, with pulled-back
+ *      label l, and with both.  The warped label image holds the
+ *      pulled-back label per voxel, 255 in no copy.
  *   R18 initialisation noise (Sec. 4.2.2, App. A.5: Gaussian kernels
  *      on both images attract the mesh points, in rounds, as long as no
  *      fold appears).  Per mesh, kernels (c_k, sigma_k, a_k) are the
@@ -106,6 +107,23 @@
  *      process.  exp is the function gexp below (range reduction by ln 2
  *      and a Taylor series, every operation one rounded IEEE operation), so
  *      positions are reproducible bit for bit.
+ *
+ * Perturbation report (test support, off by default).  R9 and R15 turn a
+ * real number into a decision (the sign of b; the nearest voxel of T(p)).
+ * A kernel that evaluates T(p) = t0 + M (p - s0) and the trilinear sample
+ * in FP32 gets the same decision unless the exact value lies within its
+ * rounding error of the threshold.  Given a relative radius gamma_pos for
+ * the position and gamma_val for the sample, the oracle bounds per voxel
+ *   eps_a = gamma_pos (|t0_a| + sum_b |M_ab| |p_b - s0_b| + 1)
+ * (M the exact linear part of the map, s0, t0 vertex 0 of the two copies)
+ * and, over the cells the box y +- eps touches,
+ *   tau = sum_a L_a eps_a + gamma_val V
+ * (L_a the largest |difference| along axis a of neighbouring stored
+ * values, V the largest |stored value|): every position within eps and
+ * every sample within tau of the exact ones.  A voxel is ambiguous when the
+ * decision is not constant over that range; its record counts it, with the
+ * spread of h it allows (R9) or the candidate labels (R15).  The report
+ * never changes a returned value.
  */
 #include <math.h>
 #include <stdint.h>
@@ -149,6 +167,8 @@ typedef struct {
     uint64_t sev;
     int32_t folded;                 /* bit 0: source copy, bit 1: target copy */
     int32_t pad;
+    int64_t amb_n[2];               /* perturbation report: ambiguous voxels (R9) */
+    double amb_slack[2];            /* and the spread of h they allow */
 } orc_tet;
 
 typedef struct {
@@ -169,6 +189,7 @@ typedef struct {
     double r;
     double *dist[2];                /* [G][N] maps of the source / target contours */
     int64_t S;                      /* 2^k */
+    double amb_pos, amb_val;        /* perturbation report radii (0: off) */
 } orc_state;
 
 /* ------------------------------------------------------------------ */
@@ -235,7 +256,23 @@ static int inside_sos(const orc_i3 v[4], orc_i3 p)
     return 1;
 }
 
-/* R4: trilinear sample as the weighted sum of the 8 cell corners. */
+/* R4: trilinear sample as the weighted sum of the 8 corners of cell i0
+ * with fractions f. */
+static double trilinear_cell(const double *img, int nx, int ny, const int i0[3], const double f[3])
+{
+    double v = 0.0;
+    for (int dz = 0; dz < 2; ++dz)
+        for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx) {
+                double w = (dx ? f[0] : 1.0 - f[0]) * (dy ? f[1] : 1.0 - f[1]) * (dz ? f[2] : 1.0 - f[2]);
+                size_t idx = ((size_t)(i0[2] + dz) * ny + (size_t)(i0[1] + dy)) * nx + (size_t)(i0[0] + dx);
+                v += w * img[idx];
+            }
+    return v;
+}
+
+/* R4 at a position y given in FP64: clamp to [0, n-1], cell
+ * i0 = min(floor(y), n - 2), fraction y - i0. */
 static double trilinear(const double *img, int nx, int ny, int nz, const double y[3])
 {
     int n[3] = {nx, ny, nz};
@@ -248,91 +285,133 @@ static double trilinear(const double *img, int nx, int ny, int nz, const double 
         i0[a] = i;
         f[a] = c - (double)i;
     }
-    double v = 0.0;
-    for (int dz = 0; dz < 2; ++dz)
-        for (int dy = 0; dy < 2; ++dy)
-            for (int dx = 0; dx < 2; ++dx) {
-                double w = (dx ? f[0] : 1.0 - f[0]) * (dy ? f[1] : 1.0 - f[1]) * (dz ? f[2] : 1.0 - f[2]);
-                size_t idx = ((size_t)(i0[2] + dz) * ny + (size_t)(i0[1] + dy)) * nx + (size_t)(i0[0] + dx);
-                v += w * img[idx];
-            }
-    return v;
+    return trilinear_cell(img, nx, ny, i0, f);
+}
+
+/* Exact rationals for the voxel-centre map (128-bit integers; gcc and
+ * clang provide them on every 64-bit target). */
+__extension__ typedef __int128 orc_i128;
+
+static orc_i128 floor_div128(orc_i128 a, orc_i128 b)   /* b > 0 */
+{
+    orc_i128 q = a / b;
+    if (a % b != 0 && a < 0) --q;
+    return q;
+}
+
+/* R4 at the exact position num[a] / den (den > 0): the clamp, the cell
+ * and whether a fraction is 0 or 1 are decided exactly; each fraction is
+ * then rounded once.  A position on a voxel centre samples that voxel's
+ * stored value exactly. */
+static double trilinear_exact(const double *img, int nx, int ny, int nz, const orc_i128 num[3], orc_i128 den)
+{
+    int n[3] = {nx, ny, nz};
+    int i0[3];
+    double f[3];
+    for (int a = 0; a < 3; ++a) {
+        orc_i128 c = num[a] < 0 ? 0 : num[a];
+        orc_i128 top = (orc_i128)(n[a] - 1) * den;
+        if (c > top) c = top;
+        orc_i128 q = c / den;
+        if (q > n[a] - 2) q = n[a] - 2;
+        i0[a] = (int)q;
+        f[a] = (double)(c - q * den) / (double)den;
+    }
+    return trilinear_cell(img, nx, ny, i0, f);
 }
 
 /* h of Sec. 4.1.2: mode 0 = squared difference; mode 1 = the printed case
- * split on foreground (> 0) and background (== 0) intensities.  b_case is
- * the value the case split looks at (R9), b the value that is compared. */
-static double h_case(int mode, double a, double b, double b_case)
+ * split on foreground (> 0) and background (== 0) intensities (R9). */
+static double h_fn(int mode, double a, double b)
 {
     if (mode == 0) return (a - b) * (a - b);
-    if (a > 0.0 && b_case > 0.0) return (a - b) * (a - b);
-    if (a == 0.0 && b_case == 0.0) return 0.0;
+    if (a > 0.0 && b > 0.0) return (a - b) * (a - b);
+    if (a == 0.0 && b == 0.0) return 0.0;
     return 1.0;
 }
 
-static double h_fn(int mode, double a, double b)
+/* ------------------------------------------------------------------ */
+/* Perturbation report (test support; see the header)                 */
+/* ------------------------------------------------------------------ */
+
+static orc_i3 orc_add(orc_i3 p, int a)
 {
-    return h_case(mode, a, b, b);
+    if (a == 0) p.x += 1; else if (a == 1) p.y += 1; else p.z += 1;
+    return p;
 }
 
-/* R9: the FP32 sample of the other image at the image of voxel (i, j, k),
- * used only to decide the case of h in mode 1. */
-/* The affine map of the GPU kernel in its FP32 arithmetic (R9, R15):
- * M = F adj(E) / D rounded to float, then y = t0 + M (p - s0) with fused
- * multiply-adds in the kernel's order, for the voxel centre (i, j, k). */
-static void map_fp32(const orc_state *st, const orc_i3 own[4], const orc_i3 oth[4], int64_t D, int64_t i,
-                     int64_t j, int64_t k, float y[3])
+/* eps[a]: the radius of position a of the map at voxel centre p. */
+static void map_radius(const orc_state *st, const orc_i3 own[4], int64_t D, const orc_i3 oth[4], orc_i3 p,
+                       double eps[3])
 {
-    int64_t e[3][3], f[3][3];
-    for (int m = 0; m < 3; ++m) {
-        e[m][0] = own[m + 1].x - own[0].x; e[m][1] = own[m + 1].y - own[0].y; e[m][2] = own[m + 1].z - own[0].z;
-        f[m][0] = oth[m + 1].x - oth[0].x; f[m][1] = oth[m + 1].y - oth[0].y; f[m][2] = oth[m + 1].z - oth[0].z;
+    double S = (double)st->S;
+    double w[4][3], g[4][3];
+    for (int i = 0; i < 4; ++i) {
+        w[i][0] = (double)oth[i].x / S - 0.5;
+        w[i][1] = (double)oth[i].y / S - 0.5;
+        w[i][2] = (double)oth[i].z / S - 0.5;
+        int64_t d0 = face_value(own, i, p);
+        for (int b = 0; b < 3; ++b)            /* d lambda_i / d p_b in voxel units */
+            g[i][b] = (double)(face_value(own, i, orc_add(p, b)) - d0) * S / (double)D;
     }
-    int64_t r[3][3];                     /* rows of adj(E): e2 x e3, e3 x e1, e1 x e2 */
-    for (int m = 0; m < 3; ++m) {
-        const int64_t *u = e[(m + 1) % 3], *v = e[(m + 2) % 3];
-        r[m][0] = u[1] * v[2] - u[2] * v[1];
-        r[m][1] = u[2] * v[0] - u[0] * v[2];
-        r[m][2] = u[0] * v[1] - u[1] * v[0];
+    double s0[3] = {(double)own[0].x / S - 0.5, (double)own[0].y / S - 0.5, (double)own[0].z / S - 0.5};
+    double pv[3] = {(double)p.x / S - 0.5, (double)p.y / S - 0.5, (double)p.z / S - 0.5};
+    for (int a = 0; a < 3; ++a) {
+        double acc = fabs(w[0][a]) + 1.0;
+        for (int b = 0; b < 3; ++b) {
+            double M = 0.0;
+            for (int i = 0; i < 4; ++i) M += w[i][a] * g[i][b];
+            acc += fabs(M) * fabs(pv[b] - s0[b]);
+        }
+        eps[a] = st->amb_pos * acc;
     }
-    const double invD = 1.0 / (double)D;
-    float M[3][3];
-    for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b)
-            M[a][b] = (float)((double)(f[0][a] * r[0][b] + f[1][a] * r[1][b] + f[2][a] * r[2][b]) * invD);
-    const float inv_s = 1.0f / (float)st->S;
-    const float s0[3] = {(float)own[0].x * inv_s - 0.5f, (float)own[0].y * inv_s - 0.5f,
-                         (float)own[0].z * inv_s - 0.5f};
-    const float t0[3] = {(float)oth[0].x * inv_s - 0.5f, (float)oth[0].y * inv_s - 0.5f,
-                         (float)oth[0].z * inv_s - 0.5f};
-    const float d[3] = {(float)i - s0[0], (float)j - s0[1], (float)k - s0[2]};
-    for (int a = 0; a < 3; ++a) y[a] = fmaf(M[a][0], d[0], fmaf(M[a][1], d[1], fmaf(M[a][2], d[2], t0[a])));
 }
 
-static float sample_fp32_case(const orc_state *st, const orc_i3 own[4], const orc_i3 oth[4], int64_t D,
-                              const double *img, int64_t i, int64_t j, int64_t k)
+/* tau: the radius of the trilinear sample of img over the positions within
+ * eps of y (R4 clamping and cells). */
+static double value_radius(const orc_state *st, const double *img, const double y[3], const double eps[3])
 {
     const orc_problem *P = &st->p;
-    float y[3];
-    map_fp32(st, own, oth, D, i, j, k, y);
-    const int n[3] = {P->nx, P->ny, P->nz};
-    float c[3], fr[3];
-    int i0[3];
+    int n[3] = {P->nx, P->ny, P->nz};
+    int c0[3], c1[3];
     for (int a = 0; a < 3; ++a) {
-        c[a] = fminf(fmaxf(y[a], 0.0f), (float)(n[a] - 1));
-        i0[a] = (int)c[a];
-        if (i0[a] > n[a] - 2) i0[a] = n[a] - 2;
-        fr[a] = c[a] - (float)i0[a];
+        double lo = fmin(fmax(y[a] - eps[a], 0.0), (double)(n[a] - 1));
+        double hi = fmin(fmax(y[a] + eps[a], 0.0), (double)(n[a] - 1));
+        c0[a] = (int)floor(lo); if (c0[a] > n[a] - 2) c0[a] = n[a] - 2;
+        c1[a] = (int)floor(hi); if (c1[a] > n[a] - 2) c1[a] = n[a] - 2;
     }
-    const size_t sy = (size_t)P->nx, sz = (size_t)P->nx * P->ny;
-    const size_t b0 = ((size_t)i0[2] * P->ny + (size_t)i0[1]) * P->nx + (size_t)i0[0];
-    float v[8];
-    for (int q = 0; q < 8; ++q)
-        v[q] = (float)img[b0 + (q & 1) + ((q >> 1) & 1) * sy + ((q >> 2) & 1) * sz];
-    const float c00 = fmaf(fr[0], v[1] - v[0], v[0]), c10 = fmaf(fr[0], v[3] - v[2], v[2]);
-    const float c01 = fmaf(fr[0], v[5] - v[4], v[4]), c11 = fmaf(fr[0], v[7] - v[6], v[6]);
-    const float c0 = fmaf(fr[1], c10 - c00, c00), c1 = fmaf(fr[1], c11 - c01, c01);
-    return fmaf(fr[2], c1 - c0, c0);
+    double V = 0.0, L[3] = {0.0, 0.0, 0.0};
+    for (int k = c0[2]; k <= c1[2] + 1; ++k)
+        for (int j = c0[1]; j <= c1[1] + 1; ++j)
+            for (int i = c0[0]; i <= c1[0] + 1; ++i) {
+                size_t idx = ((size_t)k * P->ny + (size_t)j) * P->nx + (size_t)i;
+                double v = img[idx];
+                if (fabs(v) > V) V = fabs(v);
+                if (i <= c1[0]) L[0] = fmax(L[0], fabs(img[idx + 1] - v));
+                if (j <= c1[1]) L[1] = fmax(L[1], fabs(img[idx + (size_t)P->nx] - v));
+                if (k <= c1[2]) L[2] = fmax(L[2], fabs(img[idx + (size_t)P->nx * P->ny] - v));
+            }
+    return L[0] * eps[0] + L[1] * eps[1] + L[2] * eps[2] + st->amb_val * V;
+}
+
+/* R9 report: the spread of h when the case is decided on any b' within tau
+ * of b (the compared value stays b). */
+static double h_spread(double a, double b, double tau)
+{
+    int pos = b + tau > 0.0, zero = b - tau <= 0.0 && b + tau >= 0.0, neg = b - tau < 0.0;
+    double lo = INFINITY, hi = -INFINITY, v;
+#define ORC_CASE(c, val) if (c) { v = (val); lo = fmin(lo, v); hi = fmax(hi, v); }
+    if (a > 0.0) {
+        ORC_CASE(pos, (a - b) * (a - b));
+        ORC_CASE(zero || neg, 1.0);
+    } else if (a == 0.0) {
+        ORC_CASE(zero, 0.0);
+        ORC_CASE(pos || neg, 1.0);
+    } else {
+        ORC_CASE(1, 1.0);
+    }
+#undef ORC_CASE
+    return hi - lo;
 }
 
 static int64_t floor_div(int64_t a, int64_t b)
@@ -361,6 +440,39 @@ static void bary_map(const orc_state *st, const orc_i3 own[4], int64_t D, const 
         y[1] += lam * ((double)oth[i].y / S - 0.5);
         y[2] += lam * ((double)oth[i].z / S - 0.5);
     }
+}
+
+/* The same map at a voxel centre p as an exact rational per axis,
+ * y_a = num[a] / den with den > 0: the other copy's vertices are
+ * w_i = q_i / S - 1/2 and sum_i D_i(p) = D, so
+ * y = (2 sum_i D_i(p) q_i - D S) / (2 D S). */
+static orc_i128 bary_exact(const orc_state *st, const orc_i3 own[4], int64_t D, const orc_i3 oth[4], orc_i3 p,
+                           orc_i128 num[3])
+{
+    orc_i128 sx = 0, sy = 0, sz = 0;
+    for (int i = 0; i < 4; ++i) {
+        orc_i128 di = face_value(own, i, p);
+        sx += di * oth[i].x;
+        sy += di * oth[i].y;
+        sz += di * oth[i].z;
+    }
+    orc_i128 DS = (orc_i128)D * st->S;
+    num[0] = 2 * sx - DS;
+    num[1] = 2 * sy - DS;
+    num[2] = 2 * sz - DS;
+    return 2 * DS;
+}
+
+/* R15: the voxel index nearest to num / den on an axis of n voxels, round
+ * half to even, clamped to the image; decided exactly. */
+static int64_t nearest_exact(orc_i128 num, orc_i128 den, int n)
+{
+    orc_i128 t = 2 * num + den, d2 = 2 * den;          /* y + 1/2 = t / d2 */
+    orc_i128 m = floor_div128(t, d2);
+    if (m * d2 == t && (m & 1)) m -= 1;                /* tie: y = m - 1/2, take the even neighbour */
+    if (m < 0) m = 0;
+    if (m > n - 1) m = n - 1;
+    return (int64_t)m;
 }
 
 /* One side of one tet: side 0 samples source voxels in the source copy and
@@ -401,14 +513,24 @@ static void eval_side(const orc_state *st, const orc_i3 own[4], const orc_i3 oth
             for (int64_t i = lo[0]; i <= hi[0]; ++i) {
                 orc_i3 p = {i * S + H, j * S + H, k * S + H};
                 if (!inside_sos(own, p)) continue;
-                double y[3];
-                bary_map(st, own, D, oth, p, y);
+                orc_i128 num[3];
+                orc_i128 den = bary_exact(st, own, D, oth, p, num);
+                double y[3] = {(double)num[0] / (double)den, (double)num[1] / (double)den,
+                               (double)num[2] / (double)den};
                 size_t idx = ((size_t)k * P->ny + (size_t)j) * P->nx + (size_t)i;
                 double a = img_own[idx];
-                double b = trilinear(img_oth, P->nx, P->ny, P->nz, y);
-                double b_case = P->h_mode == 1 ? (double)sample_fp32_case(st, own, oth, D, img_oth, i, j, k) : b;
-                e_img += h_case(P->h_mode, a, b, b_case);
+                double b = trilinear_exact(img_oth, P->nx, P->ny, P->nz, num, den);
+                e_img += h_fn(P->h_mode, a, b);
                 nv += 1;
+                if (P->h_mode == 1 && st->amb_pos > 0.0) {     /* perturbation report (R9) */
+                    double eps[3];
+                    map_radius(st, own, D, oth, p, eps);
+                    double tau = value_radius(st, img_oth, y, eps);
+                    if (tau > 0.0 && fabs(b) <= tau) {
+                        rec->amb_n[side] += 1;
+                        rec->amb_slack[side] += h_spread(a, b, tau);
+                    }
+                }
                 if (P->g_mode == 0) {
                     for (int g = 0; g < st->G; ++g) {
                         double dg = st->dist[side][(size_t)g * ((size_t)P->nx * P->ny * P->nz) + idx];
@@ -814,6 +936,13 @@ int orc_setup(const orc_problem *P, orc_state **out)
     return ORC_OK;
 }
 
+/* Turn the perturbation report on (radii > 0) or off (0). */
+void orc_set_perturbation(orc_state *st, double gamma_pos, double gamma_val)
+{
+    st->amb_pos = gamma_pos > 0.0 ? gamma_pos : 0.0;
+    st->amb_val = gamma_val > 0.0 ? gamma_val : 0.0;
+}
+
 /* accessors used by the tests */
 int orc_n_groups(const orc_state *st) { return st->G; }
 double orc_radius(const orc_state *st) { return st->r; }
@@ -995,8 +1124,22 @@ double orc_repair_sigma(const orc_state *st, const float *X, int v, double scale
 /* R15: displacement field and label overlap                           */
 /* ------------------------------------------------------------------ */
 
+/* R15: the voxel index nearest to position y on an axis of n voxels
+ * (round half to even, clamped to the image). */
+static int64_t nearest_index(double y, int n)
+{
+    double r = rint(y);
+    if (!(r >= 0.0)) r = 0.0;
+    if (r > (double)(n - 1)) r = (double)(n - 1);
+    return (int64_t)r;
+}
+
+/* cand (optional, [N][8]): the labels the perturbation report allows per
+ * covered voxel (all eight equal the pulled-back label where the nearest
+ * voxel is the same over the whole range). */
 int orc_dvf(const orc_state *st, const float *src, const float *tgt, int side, double *dvf,
-            const uint8_t *lab_own, const uint8_t *lab_oth, int n_labels, int64_t *counts, uint8_t *warped)
+            const uint8_t *lab_own, const uint8_t *lab_oth, int n_labels, int64_t *counts, uint8_t *warped,
+            uint8_t *cand)
 {
     const orc_problem *P = &st->p;
     const size_t N = (size_t)P->nx * P->ny * P->nz;
@@ -1006,6 +1149,7 @@ int orc_dvf(const orc_state *st, const float *src, const float *tgt, int side, d
         for (size_t q = 0; q < 3 * N; ++q) dvf[q] = NAN;
     if (counts) memset(counts, 0, sizeof(int64_t) * 3 * (size_t)n_labels);
     if (warped) memset(warped, 255, N);                   /* 255: in no copy */
+    if (cand) memset(cand, 255, 8 * N);
     const float *Xo = side == 0 ? src : tgt, *Xt = side == 0 ? tgt : src;
     int64_t S = st->S, H = st->S / 2;
     int n[3] = {P->nx, P->ny, P->nz};
@@ -1039,26 +1183,35 @@ int orc_dvf(const orc_state *st, const float *src, const float *tgt, int side, d
                     size_t idx = ((size_t)k * P->ny + (size_t)j) * P->nx + (size_t)i;
                     if (covered[idx]) continue;
                     covered[idx] = 1;
+                    orc_i128 num[3];
+                    orc_i128 den = bary_exact(st, own, D, oth, p, num);
+                    double y[3] = {(double)num[0] / (double)den, (double)num[1] / (double)den,
+                                   (double)num[2] / (double)den};
                     if (dvf) {
-                        double y[3];
-                        bary_map(st, own, D, oth, p, y);
                         dvf[3 * idx] = y[0] - (double)i;
                         dvf[3 * idx + 1] = y[1] - (double)j;
                         dvf[3 * idx + 2] = y[2] - (double)k;
                     }
                     if (counts || warped) {
-                        float y32[3];
-                        map_fp32(st, own, oth, D, i, j, k, y32);
                         int64_t m[3];
-                        for (int a = 0; a < 3; ++a) {
-                            float r = rintf(y32[a]);
-                            if (!(r >= 0.0f)) r = 0.0f;
-                            if (r > (float)(n[a] - 1)) r = (float)(n[a] - 1);
-                            m[a] = (int64_t)r;
-                        }
+                        for (int a = 0; a < 3; ++a) m[a] = nearest_exact(num[a], den, n[a]);
                         size_t jdx = ((size_t)m[2] * P->ny + (size_t)m[1]) * P->nx + (size_t)m[0];
                         int lb = lab_oth[jdx];
                         if (warped) warped[idx] = (uint8_t)lb;
+                        if (cand) {                           /* perturbation report (R15) */
+                            int64_t c[3][2];
+                            double eps[3] = {0.0, 0.0, 0.0};
+                            if (st->amb_pos > 0.0) map_radius(st, own, D, oth, p, eps);
+                            for (int a = 0; a < 3; ++a) {
+                                c[a][0] = nearest_index(y[a] - eps[a], n[a]);
+                                c[a][1] = nearest_index(y[a] + eps[a], n[a]);
+                            }
+                            for (int q = 0; q < 8; ++q) {
+                                size_t cdx = ((size_t)c[2][(q >> 2) & 1] * P->ny + (size_t)c[1][(q >> 1) & 1]) * P->nx +
+                                             (size_t)c[0][q & 1];
+                                cand[8 * idx + q] = lab_oth[cdx];
+                            }
+                        }
                         if (!counts) continue;
                         int la = lab_own[idx];
                         if (la < n_labels) counts[3 * la] += 1;

@@ -1,7 +1,9 @@
 """GPU parity of the displacement field and label overlap (reading R15)
-against the oracle: the covered voxels (the NaN pattern) and the label
-counts are exact; displacements are the FP32 affine map against the FP64
-barycentric map, within 1e-4 voxel."""
+against the oracle: the covered voxels (the NaN pattern) are exact;
+displacements are the FP32 affine map against the FP64 barycentric map,
+within 1e-4 voxel; the label counts agree with the oracle's exact pull-back
+except at voxels whose nearest voxel the FP32 error bound leaves open
+(helpers.check_warped_labels)."""
 
 import numpy as np
 import pytest
@@ -9,7 +11,7 @@ import torch
 
 import oracle
 import synth
-from helpers import box_lattice, problem, random_image
+from helpers import box_lattice, check_warped_labels, problem, random_image
 
 pytestmark = pytest.mark.gpu
 
@@ -36,7 +38,11 @@ def compare(mo, p, src, tgt, side, n_labels=5, seed=0):
     np.testing.assert_array_equal(np.isnan(dvf), np.isnan(want))
     cov = ~np.isnan(want)
     np.testing.assert_allclose(dvf[cov], want[cov], rtol=0, atol=1e-4)
-    np.testing.assert_array_equal(counts, wc)
+    w = gp.warp_labels(torch.as_tensor(src).cuda(), torch.as_tensor(tgt).cuda(), side,
+                       torch.as_tensor(lab_oth).cuda()).cpu().numpy()
+    _, amb = check_warped_labels(w, orc, src, tgt, side, lab_oth, n_labels, counts, lab_own)
+    if not amb.any():                 # then the oracle's own counts hold exactly
+        np.testing.assert_array_equal(counts, wc)
     return dvf, counts
 
 

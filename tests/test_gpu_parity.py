@@ -10,7 +10,7 @@ import torch
 
 import oracle
 import synth
-from helpers import box_lattice, problem, random_image
+from helpers import GAMMA_POS, GAMMA_VAL, MAX_AMBIGUOUS, box_lattice, problem, random_image
 
 pytestmark = pytest.mark.gpu
 
@@ -41,10 +41,18 @@ def assert_obj_close(g, o, what=""):
 
 
 def check_against_oracle(mo, prob, idx=None, **over):
-    """Full evaluation of prob.sol_src/sol_tgt on the GPU; oracle on ``idx``."""
+    """Full evaluation of prob.sol_src/sol_tgt on the GPU; oracle on ``idx``.
+
+    In the foreground/background mode of h the oracle decides each case on
+    the exact sample (R9).  Voxels whose exact sample lies within the FP32
+    error bound of 0 (helpers.GAMMA_*) are ambiguous: a tet's e_img may then
+    differ by the spread of h they allow (``amb_slack``) on top of the FP32
+    rounding tolerance; every other voxel must take the oracle's case.  The
+    ambiguous voxels must stay below MAX_AMBIGUOUS of the covered ones."""
     n = prob.sol_src.shape[0]
     gp = mo.Problem(prob, max_solutions=n, **over)
     orc = oracle.Oracle(prob, **{**over, "subvoxel_bits": gp.subvoxel_bits, "trunc_radius": gp.trunc_radius})
+    orc.set_perturbation(GAMMA_POS, GAMMA_VAL)
     obj, folded, sev = gpu_full(gp, prob.sol_src, prob.sol_tgt)
     recs = gp.read_records(n)
     for i in (range(n) if idx is None else idx):
@@ -54,11 +62,19 @@ def check_against_oracle(mo, prob, idx=None, **over):
         np.testing.assert_array_equal(recs[i]["n_gp"], ot["n_gp"])
         np.testing.assert_array_equal(recs[i]["folded"], ot["folded"])
         np.testing.assert_array_equal(recs[i]["sev"], ot["sev"])
-        np.testing.assert_allclose(recs[i]["e_img"], ot["e_img"], rtol=RTOL_TET, atol=1e-3)
+        slack = ot["amb_slack"]
+        assert ot["amb_n"].sum() <= MAX_AMBIGUOUS * max(1, ot["n_vox"].sum()), "too many ambiguous voxels"
+        err = np.abs(recs[i]["e_img"].astype(np.float64) - ot["e_img"])
+        assert (err <= RTOL_TET * np.abs(ot["e_img"]) + 1e-3 + slack).all(), f"e_img of solution {i}"
         np.testing.assert_allclose(recs[i]["e_mag"], ot["e_mag"], rtol=RTOL_TET, atol=1e-9)
         assert int(folded[i]) == r["folded"]
         assert sev[i] == r["severity"]
-        assert_obj_close(obj[i], r["obj"], f"solution {i}")
+        total_slack = slack.sum() / max(1, r["n_vox"])
+        if total_slack == 0.0:
+            assert_obj_close(obj[i], r["obj"], f"solution {i}")
+        else:
+            assert abs(obj[i][0] - r["obj"][0]) <= RTOL_OBJ * abs(r["obj"][0]) + total_slack, f"solution {i}"
+            assert_obj_close(np.r_[r["obj"][0], obj[i][1:]], r["obj"], f"solution {i}")
     return gp, orc, obj
 
 

@@ -1,7 +1,10 @@
 """GPU parity of the warped label image and of the surface distances
 (reading R17, Hausdorff distance and its 95th percentile, Sec. 5) against
-the oracle.  Both are exact: warped labels equal element by element, and
-HD / HD95 are square roots of integers, so they equal bit for bit."""
+the oracle.  Warped labels equal the oracle's exact pull-back element by
+element, except at voxels whose nearest voxel the FP32 error bound leaves
+open, which must hold one of the labels it allows
+(helpers.check_warped_labels).  HD / HD95 of the same label images are
+square roots of integers, so they equal bit for bit."""
 
 import math
 
@@ -11,6 +14,7 @@ import torch
 
 import oracle
 import synth
+from helpers import check_warped_labels
 from oracle import surface as sd
 
 pytestmark = pytest.mark.gpu
@@ -101,8 +105,7 @@ def test_warped_labels_c0(mo, side):
     for i in range(3):
         w = gp.warp_labels(torch.as_tensor(p.sol_src[i]).cuda(), torch.as_tensor(p.sol_tgt[i]).cuda(), side,
                            torch.as_tensor(oth).cuda()).cpu().numpy()
-        want = orc.warp_labels(p.sol_src[i], p.sol_tgt[i], side, oth)
-        np.testing.assert_array_equal(w, want)
+        check_warped_labels(w, orc, p.sol_src[i], p.sol_tgt[i], side, oth)
         for label in (1, 2, 3):
             check(mo, own, w, label)
 
@@ -117,8 +120,7 @@ def test_partial_mesh_marks_uncovered(mo):
     tgt = (pts + 0.75).astype(np.float32)
     w = gp.warp_labels(torch.as_tensor(pts).cuda(), torch.as_tensor(tgt).cuda(), 0,
                        torch.as_tensor(lab).cuda()).cpu().numpy()
-    want = oracle.Oracle(p, subvoxel_bits=gp.subvoxel_bits).warp_labels(pts, tgt, 0, lab)
-    np.testing.assert_array_equal(w, want)
+    check_warped_labels(w, oracle.Oracle(p, subvoxel_bits=gp.subvoxel_bits), pts, tgt, 0, lab)
     assert (w == mo.NO_LABEL).any() and (w != mo.NO_LABEL).any()
 
 
@@ -131,7 +133,7 @@ def test_full_size_registration_scores(mo):
     orc = oracle.Oracle(p, subvoxel_bits=gp.subvoxel_bits)
     w = gp.warp_labels(torch.as_tensor(p.sol_src[1]).cuda(), torch.as_tensor(p.sol_tgt[1]).cuda(), 0,
                        torch.as_tensor(lb).cuda())
-    want = orc.warp_labels(p.sol_src[1], p.sol_tgt[1], 0, lb)
-    np.testing.assert_array_equal(w.cpu().numpy(), want)
+    w = w.cpu().numpy()
+    check_warped_labels(w, orc, p.sol_src[1], p.sol_tgt[1], 0, lb)
     for label in range(1, 6):
-        check(mo, la, want, label)
+        check(mo, la, w, label)
