@@ -551,13 +551,18 @@ morea_status morea_profile_read(morea_problem *p, double *raster_ms, int64_t *la
  * -- and so cannot create a problem handle either.
  *   tets        device [n_tets][4] vertex ids in [0, n_points) (any
  *               orientation: a tet whose reference volume is negative is
- *               re-ordered, as at problem creation; the reference volume must
- *               be nonzero).  A tet with an id out of range is not read: its
- *               solution gets f_mag = NaN and folded = 1.
+ *               re-ordered, as at problem creation).  A tet with an id out of
+ *               range, or with a zero reference volume (which problem
+ *               creation rejects), is not evaluated: every solution gets
+ *               f_mag = NaN and folded = 1.
  *   ref_points  device [n_points][3] initial mesh (gives the reference signs)
  *   cdelta      device [n_tets] elasticity factor of each tet
- *   nx, ny, nz, subvoxel_bits   image box and snapping grid, as in
- *               morea_problem_desc (subvoxel_bits 0 means 8)
+ *   nx, ny, nz, subvoxel_bits   image box and snapping grid, chosen exactly
+ *               as morea_create_problem chooses them: subvoxel_bits 0 takes
+ *               the largest k <= 8 with max(nx, ny, nz) 2^k <= 65536 and
+ *               4 n_tets nx ny nz 8^k < 2^63 (the exact 64-bit severity
+ *               sum); a given k that breaks either bound returns
+ *               MOREA_EINVAL
  *   src_pts, tgt_pts  device [n_sol][n_points][3]
  *   f_mag       device [n_sol] out: f_magnitude (obj[1] of morea_eval_full)
  *   folded      device [n_sol] out; severity device [n_sol] out or NULL
@@ -569,6 +574,8 @@ morea_status morea_profile_read(morea_problem *p, double *raster_ms, int64_t *la
  * race and give wrong results; calls on one stream are safe.  The first call
  * on each device looks up the array's device address (cudaGetSymbolAddress)
  * with that device current; make that first call before any stream capture.
+ * The address is kept for the life of the process, so the entry point is not
+ * supported on a device after cudaDeviceReset of that device.
  * Nothing is allocated and no memory of the caller is kept. */
 morea_status morea_fold_magnitude_noalloc(int32_t n_sol, int32_t n_points, int32_t n_tets,
                                           const int32_t *tets, const float *ref_points,

@@ -36,6 +36,9 @@ void *g_noalloc_addr[kMaxDevices] = {nullptr};
 // Device address of the scratch array on the current device, looked up once
 // per device.  In host code g_noalloc_scratch names a host-side shadow, not
 // device memory, so the kernels get the address from cudaGetSymbolAddress.
+// The address is cached for the life of the process: after cudaDeviceReset
+// on a device the cached value is stale, so the entry point is not
+// supported on that device after a reset.
 cudaError_t noalloc_scratch(TetOut **out)
 {
     int dev = 0;
@@ -73,11 +76,21 @@ __global__ void __launch_bounds__(kBlock) k_tet_noalloc(DevProblem P, int n_sol,
             continue;
         }
         // same orientation rule as problem creation: swap the last two
-        // vertices of a tet whose reference volume is negative
+        // vertices of a tet whose reference volume is negative; a zero
+        // reference volume (rejected at problem creation) gives NaN / folded
         int4 qr[4];
 #pragma unroll
         for (int m = 0; m < 4; ++m) qr[m] = snap3(ref + 3 * (size_t)v[m], P);
-        if (orient_d(qr[0], qr[1], qr[2], qr[3]) < 0.0) {
+        const double dref = orient_d(qr[0], qr[1], qr[2], qr[3]);
+        if (dref == 0.0) {
+            TetOut bad;
+            bad.e_mag = __int_as_float(0x7fc00000);
+            bad.folded = 3u;
+            bad.sev = 0ull;
+            scratch[e] = bad;
+            continue;
+        }
+        if (dref < 0.0) {
             const int tmp = v[2];
             v[2] = v[3];
             v[3] = tmp;
@@ -155,9 +168,10 @@ extern "C" morea_status morea_fold_magnitude_noalloc(int32_t n_sol, int32_t n_po
         !f_mag || !folded)
         return MOREA_EINVAL;
     if (nx < 2 || ny < 2 || nz < 2) return MOREA_EINVAL;
-    const int k = subvoxel_bits == 0 ? 8 : subvoxel_bits;
-    const long long nmax = std::max(nx, std::max(ny, nz));
-    if (k < 2 || k > 14 || (nmax << k) > 65536) return MOREA_EINVAL;
+    // the same grid as morea_create_problem: the box limit and the 64-bit
+    // severity bound, with 0 picking the largest k <= 8 that meets both
+    const int k = choose_subvoxel_bits(subvoxel_bits, nx, ny, nz, n_tets);
+    if (k < 0) return MOREA_EINVAL;
     // the scratch holds MOREA_NOALLOC_MAX_TET_EVALS (solution, tet) records
     if ((long long)n_sol * n_tets > (long long)MOREA_NOALLOC_MAX_TET_EVALS) return MOREA_EINVAL;
     TetOut *scratch = nullptr;

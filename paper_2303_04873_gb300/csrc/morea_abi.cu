@@ -35,6 +35,26 @@ bool severity_fits(long long T, long long N, int k)
     return std::log2(4.0) + std::log2((double)T) + std::log2((double)N) + 3.0 * k < 63.0;
 }
 
+}  // namespace
+
+// Snapping grid 2^-k of a problem (reading R1): a requested k must keep
+// max(n) 2^k <= 65536 and the exact severity sum in 64 bits; 0 asks for the
+// largest k <= 8 that does.  Returns -1 when no k qualifies.
+int morea::choose_subvoxel_bits(int requested, int nx, int ny, int nz, long long n_tets)
+{
+    const long long nmax = std::max(nx, std::max(ny, nz));
+    const long long N = (long long)nx * ny * nz;
+    int k = requested;
+    if (k == 0) {
+        k = 8;
+        while (k > 2 && ((nmax << k) > 65536 || !severity_fits(n_tets, N, k))) --k;
+    }
+    if (k < 2 || k > 14 || (nmax << k) > 65536 || !severity_fits(n_tets, N, k)) return -1;
+    return k;
+}
+
+namespace {
+
 morea_status from_cuda(cudaError_t e) { return e == cudaSuccess ? MOREA_OK : MOREA_ECUDA; }
 
 // Rasterisation launch wrapped by the optional instrumentation.
@@ -116,15 +136,10 @@ morea_status morea_create_problem(const morea_problem_desc *d, void *stream, mor
         return MOREA_EINVAL;
     if (d->tissue_factor && d->n_labels < 1) return MOREA_EINVAL;
     const int nx = d->nx, ny = d->ny, nz = d->nz;
-    const int nmax = std::max(nx, std::max(ny, nz));
     const long long N = (long long)nx * ny * nz;
     const int V = d->n_points, T = d->n_tets;
-    int k = d->subvoxel_bits;
-    if (k == 0) {
-        k = 8;
-        while (k > 2 && ((long long)nmax << k > 65536 || !severity_fits(T, N, k))) --k;
-    }
-    if (k < 2 || k > 14 || ((long long)nmax << k) > 65536 || !severity_fits(T, N, k)) return MOREA_EINVAL;
+    const int k = choose_subvoxel_bits(d->subvoxel_bits, nx, ny, nz, T);
+    if (k < 0) return MOREA_EINVAL;
     int G = 0;
     for (int m = 0; m < d->n_guid; ++m) {
         const int g = d->guid_group ? d->guid_group[m] : 0;

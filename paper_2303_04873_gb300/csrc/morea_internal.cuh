@@ -226,5 +226,9 @@ cudaError_t launch_partial_features(const DevProblem *dp, int n_req, const int *
 
 int sm_count();
 size_t partial_smem_bytes(int n_tets, int max_changed);
+// Snapping grid of reading R1 for an image box and tet count: the requested
+// k if it keeps coordinates below 2^16 and the exact severity sum in 64
+// bits, else -1; 0 picks the largest such k <= 8 (morea_abi.cu).
+int choose_subvoxel_bits(int requested, int nx, int ny, int nz, long long n_tets);
 
 }  // namespace morea

@@ -174,3 +174,22 @@ def test_surface_distance_arguments_checked_on_host(mo):
     args[6] = ctypes.c_void_p(256 + 16)   # workspace not 256-byte aligned
     assert L.morea_surface_distance(*args) == mo.EINVAL
     assert L.morea_warp_labels(None, fake, fake, 0, fake, fake, None) == mo.EINVAL
+
+
+def test_noalloc_grid_checked_on_host(mo):
+    """morea_fold_magnitude_noalloc applies problem creation's grid bounds
+    before touching the GPU: an explicit k whose exact 64-bit severity sum
+    could overflow (4 T N 8^k >= 2^63) or whose box exceeds 2^16 snapped
+    units is rejected."""
+    L = mo.lib()
+    fake = ctypes.c_void_p(256)        # never dereferenced: the host checks fail first
+    T = mo.NOALLOC_MAX_TET_EVALS
+
+    def call(n_tets, box, k):
+        return L.morea_fold_magnitude_noalloc(1, 4, n_tets, fake, fake, fake, *box, k, fake, fake, fake, fake,
+                                              None, None)
+
+    assert call(T, (256, 256, 160), 8) == mo.EINVAL          # 4 T N 8^8 ~ 2^68
+    assert call(16, (512, 8, 8), 8) == mo.EINVAL             # 512 * 2^8 > 2^16
+    assert call(16, (8, 8, 8), 15) == mo.EINVAL
+    assert call(T + 1, (8, 8, 8), 0) == mo.EINVAL            # beyond the scratch

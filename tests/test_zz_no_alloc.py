@@ -19,6 +19,7 @@ import pytest
 import torch
 
 import synth
+from helpers import box_lattice, problem, random_image
 
 pytestmark = pytest.mark.gpu
 
@@ -78,3 +79,53 @@ def test_noalloc_rejects_batches_beyond_its_scratch():
            torch.empty(n, dtype=torch.float64, device="cuda"))
     rc = _noalloc(mo, p, 8, src, src, *out)
     assert rc == mo.EINVAL
+
+
+def test_noalloc_chooses_the_grid_of_problem_creation():
+    """subvoxel_bits = 0 picks the same grid as problem creation: on a
+    512-voxel-long box both lower k from 8 to 7."""
+    from paper_2303_04873_gb300 import build
+    build.build()
+    from paper_2303_04873_gb300 import morea as mo
+    nx, ny, nz = 512, 6, 5
+    pts, tets = box_lattice(np.linspace(-0.5, nx - 0.5, 9), [-0.5, 2.0, ny - 0.5], [-0.5, nz - 0.5])
+    rng = np.random.default_rng(11)
+    sols = np.repeat(pts[None], 4, axis=0).astype(np.float64)
+    ix = (pts[:, 0] > -0.5) & (pts[:, 0] < nx - 0.5)          # off the x faces: move along x
+    iy = pts[:, 1] == np.float32(2.0)                           # the inner y level: move along y
+    sols[:, ix, 0] += rng.uniform(-3.0, 3.0, size=(4, int(ix.sum())))
+    sols[:, iy, 1] += rng.uniform(-0.4, 0.4, size=(4, int(iy.sum())))
+    img = random_image((nz, ny, nx), 3)
+    p = problem(img, img, pts, tets, subvoxel_bits=0, sol_src=sols.astype(np.float32),
+                sol_tgt=sols[::-1].copy().astype(np.float32))
+    gp = mo.Problem(p, max_solutions=4)
+    assert gp.subvoxel_bits == 7
+    src, tgt = torch.as_tensor(p.sol_src).cuda(), torch.as_tensor(p.sol_tgt).cuda()
+    obj, folded_ref, sev_ref = gp.eval_full(src, tgt)
+    p.n_solutions = 4
+    out = (torch.empty(4, dtype=torch.float64, device="cuda"), torch.empty(4, dtype=torch.uint8, device="cuda"),
+           torch.empty(4, dtype=torch.float64, device="cuda"))
+    assert _noalloc(mo, p, 0, src, tgt, *out) == mo.OK
+    np.testing.assert_array_equal(out[1].cpu().numpy(), folded_ref.cpu().numpy())
+    np.testing.assert_array_equal(out[2].cpu().numpy(), sev_ref.cpu().numpy())
+    np.testing.assert_allclose(out[0].cpu().numpy(), obj[:, 1].cpu().numpy(), rtol=1e-5, atol=0)
+    gp.close()
+
+
+def test_noalloc_reports_a_zero_reference_volume():
+    """A tet whose reference volume is zero (problem creation rejects it) is
+    not evaluated: every solution reports f_magnitude NaN and folded."""
+    from paper_2303_04873_gb300 import build
+    build.build()
+    from paper_2303_04873_gb300 import morea as mo
+    p = synth.make_c0(n_sol=3)
+    ref = p.ref_points.copy()
+    t0 = p.tets[5]
+    ref[t0[3]] = ref[t0[0]]                 # collapse the tet onto a triangle
+    p.ref_points = ref
+    src, tgt = torch.as_tensor(p.sol_src).cuda(), torch.as_tensor(p.sol_tgt).cuda()
+    out = (torch.zeros(3, dtype=torch.float64, device="cuda"), torch.zeros(3, dtype=torch.uint8, device="cuda"),
+           torch.zeros(3, dtype=torch.float64, device="cuda"))
+    assert _noalloc(mo, p, 8, src, tgt, *out) == mo.OK
+    assert np.isnan(out[0].cpu().numpy()).all()
+    assert (out[1].cpu().numpy() == 1).all()
