@@ -340,58 +340,106 @@ static orc_i3 orc_add(orc_i3 p, int a)
     return p;
 }
 
-/* eps[a]: the radius of position a of the map at voxel centre p. */
+/* eps[a]: the radius of position a of the map at voxel centre p.  A row
+ * of the map whose exact entries M_ab are all in {-1, 0, 1} is evaluated
+ * exactly in FP32 (the products and sums of 2^-k-grid values below 2^10
+ * need at most 18 bits), so its radius is 0. */
 static void map_radius(const orc_state *st, const orc_i3 own[4], int64_t D, const orc_i3 oth[4], orc_i3 p,
                        double eps[3])
 {
     double S = (double)st->S;
-    double w[4][3], g[4][3];
+    int64_t g[4][3];                           /* d D_i / d p_b per snapped unit (integers) */
     for (int i = 0; i < 4; ++i) {
-        w[i][0] = (double)oth[i].x / S - 0.5;
-        w[i][1] = (double)oth[i].y / S - 0.5;
-        w[i][2] = (double)oth[i].z / S - 0.5;
         int64_t d0 = face_value(own, i, p);
-        for (int b = 0; b < 3; ++b)            /* d lambda_i / d p_b in voxel units */
-            g[i][b] = (double)(face_value(own, i, orc_add(p, b)) - d0) * S / (double)D;
+        for (int b = 0; b < 3; ++b) g[i][b] = face_value(own, i, orc_add(p, b)) - d0;
     }
     double s0[3] = {(double)own[0].x / S - 0.5, (double)own[0].y / S - 0.5, (double)own[0].z / S - 0.5};
     double pv[3] = {(double)p.x / S - 0.5, (double)p.y / S - 0.5, (double)p.z / S - 0.5};
     for (int a = 0; a < 3; ++a) {
-        double acc = fabs(w[0][a]) + 1.0;
+        double t0 = (a == 0 ? oth[0].x : a == 1 ? oth[0].y : oth[0].z) / S - 0.5;
+        double acc = fabs(t0) + 1.0;
+        int unit_row = 1;
         for (int b = 0; b < 3; ++b) {
-            double M = 0.0;
-            for (int i = 0; i < 4; ++i) M += w[i][a] * g[i][b];
-            acc += fabs(M) * fabs(pv[b] - s0[b]);
+            /* M_ab = sum_i q_i,a g_i,b / D exactly (the -1/2 offsets cancel: sum_i g_i = 0) */
+            orc_i128 num = 0;
+            for (int i = 0; i < 4; ++i) {
+                int64_t q = a == 0 ? oth[i].x : a == 1 ? oth[i].y : oth[i].z;
+                num += (orc_i128)q * g[i][b];
+            }
+            if (!(num == 0 || num == D || num == -(orc_i128)D)) unit_row = 0;
+            acc += fabs((double)num / (double)D) * fabs(pv[b] - s0[b]);
         }
-        eps[a] = st->amb_pos * acc;
+        eps[a] = unit_row ? 0.0 : st->amb_pos * acc;
     }
 }
 
 /* tau: the radius of the trilinear sample of img over the positions within
- * eps of y (R4 clamping and cells). */
-static double value_radius(const orc_state *st, const double *img, const double y[3], const double eps[3])
+ * eps of y (R4 clamping and cells).  fix[a] >= 0 marks an axis whose
+ * clamped position is the grid index fix[a] in every evaluation within eps
+ * (see exact_axes).  On such an axis the fraction is 0 (fix[a] <= n - 2) or
+ * 1 (fix[a] = n - 1, cell n - 2): the corner fix[a] carries the whole
+ * weight.  With fraction 0 an FP32 lerp returns that corner exactly; with
+ * fraction 1 it reads the other corner too, which then counts for the
+ * rounding part.  If every corner that can carry weight is 0, the exact
+ * sample is 0 and so is every FP32 evaluation within eps (a lerp of zeros
+ * is 0, and fmaf(1, 0 - v, v) is 0): the radius is 0. */
+static double value_radius(const orc_state *st, const double *img, const double y[3], const double eps[3],
+                           const int fix[3])
 {
     const orc_problem *P = &st->p;
     int n[3] = {P->nx, P->ny, P->nz};
-    int c0[3], c1[3];
+    int r0[3], r1[3], w0[3], w1[3];          /* corners read (rounding) and corners with weight */
     for (int a = 0; a < 3; ++a) {
+        if (fix[a] >= 0) {
+            w0[a] = w1[a] = fix[a];
+            r0[a] = fix[a] == n[a] - 1 ? n[a] - 2 : fix[a];
+            r1[a] = fix[a];
+            continue;
+        }
         double lo = fmin(fmax(y[a] - eps[a], 0.0), (double)(n[a] - 1));
         double hi = fmin(fmax(y[a] + eps[a], 0.0), (double)(n[a] - 1));
-        c0[a] = (int)floor(lo); if (c0[a] > n[a] - 2) c0[a] = n[a] - 2;
-        c1[a] = (int)floor(hi); if (c1[a] > n[a] - 2) c1[a] = n[a] - 2;
+        int c0 = (int)floor(lo), c1 = (int)floor(hi);
+        if (c0 > n[a] - 2) c0 = n[a] - 2;
+        if (c1 > n[a] - 2) c1 = n[a] - 2;
+        r0[a] = w0[a] = c0;
+        r1[a] = w1[a] = c1 + 1;
     }
     double V = 0.0, L[3] = {0.0, 0.0, 0.0};
-    for (int k = c0[2]; k <= c1[2] + 1; ++k)
-        for (int j = c0[1]; j <= c1[1] + 1; ++j)
-            for (int i = c0[0]; i <= c1[0] + 1; ++i) {
+    int weighted_nonzero = 0;
+    for (int k = r0[2]; k <= r1[2]; ++k)
+        for (int j = r0[1]; j <= r1[1]; ++j)
+            for (int i = r0[0]; i <= r1[0]; ++i) {
                 size_t idx = ((size_t)k * P->ny + (size_t)j) * P->nx + (size_t)i;
                 double v = img[idx];
                 if (fabs(v) > V) V = fabs(v);
-                if (i <= c1[0]) L[0] = fmax(L[0], fabs(img[idx + 1] - v));
-                if (j <= c1[1]) L[1] = fmax(L[1], fabs(img[idx + (size_t)P->nx] - v));
-                if (k <= c1[2]) L[2] = fmax(L[2], fabs(img[idx + (size_t)P->nx * P->ny] - v));
+                if (v != 0.0 && i >= w0[0] && i <= w1[0] && j >= w0[1] && j <= w1[1] && k >= w0[2] && k <= w1[2])
+                    weighted_nonzero = 1;
+                if (fix[0] < 0 && i < r1[0]) L[0] = fmax(L[0], fabs(img[idx + 1] - v));
+                if (fix[1] < 0 && j < r1[1]) L[1] = fmax(L[1], fabs(img[idx + (size_t)P->nx] - v));
+                if (fix[2] < 0 && k < r1[2]) L[2] = fmax(L[2], fabs(img[idx + (size_t)P->nx * P->ny] - v));
             }
-    return L[0] * eps[0] + L[1] * eps[1] + L[2] * eps[2] + st->amb_val * V;
+    double tau = 0.0;
+    for (int a = 0; a < 3; ++a)
+        if (fix[a] < 0) tau += L[a] * eps[a];
+    return weighted_nonzero ? tau + st->amb_val * V : 0.0;
+}
+
+/* fix[a] of value_radius: the grid index at which the clamped position
+ * sits in every evaluation within eps -- an exact integer with eps[a] = 0,
+ * or a range that clamps as a whole to 0 or to n - 1 -- else -1. */
+static void exact_axes(const orc_i128 num[3], orc_i128 den, const int n[3], const double y[3], const double eps[3],
+                       int fix[3])
+{
+    for (int a = 0; a < 3; ++a) {
+        fix[a] = -1;
+        if (y[a] + eps[a] <= 0.0) { fix[a] = 0; continue; }
+        if (y[a] - eps[a] >= (double)(n[a] - 1)) { fix[a] = n[a] - 1; continue; }
+        if (eps[a] != 0.0) continue;
+        orc_i128 c = num[a] < 0 ? 0 : num[a];
+        orc_i128 top = (orc_i128)(n[a] - 1) * den;
+        if (c > top) c = top;
+        if (c % den == 0) fix[a] = (int)(c / den);
+    }
 }
 
 /* R9 report: the spread of h when the case is decided on any b' within tau
@@ -524,8 +572,10 @@ static void eval_side(const orc_state *st, const orc_i3 own[4], const orc_i3 oth
                 nv += 1;
                 if (P->h_mode == 1 && st->amb_pos > 0.0) {     /* perturbation report (R9) */
                     double eps[3];
+                    int fix[3];
                     map_radius(st, own, D, oth, p, eps);
-                    double tau = value_radius(st, img_oth, y, eps);
+                    exact_axes(num, den, n, y, eps, fix);
+                    double tau = value_radius(st, img_oth, y, eps, fix);
                     if (tau > 0.0 && fabs(b) <= tau) {
                         rec->amb_n[side] += 1;
                         rec->amb_slack[side] += h_spread(a, b, tau);

@@ -4,13 +4,14 @@ and R15): the decisions it marks as open under the FP32 error model of
 evaluation written here in numpy.
 
 - The report never changes a returned value, and is all zero when off.
-- Integer translation, foreground/background h: a voxel is ambiguous exactly
-  when its sample is a stored 0 with a nonzero value in the 3x3x3
-  neighbourhood of its mapped position; the spread is |a^2 - 1| (a > 0) or
-  1 (a = 0).
-- Half-voxel translation, labels: every covered voxel whose mapped x lies on
-  an interior half-integer allows both neighbours; an integer translation
-  leaves every voxel's label fixed, equal to the label at p + t.
+- An integer translation (map rows in {-1, 0, 1}) is exact in FP32: nothing
+  is open, and the labels are those at p + t.
+- A doubling map, foreground/background h: a voxel is open exactly when its
+  sample is a stored 0 with a nonzero value in the 3x3x3 neighbourhood of
+  its mapped position; the spread is |a^2 - 1| (a > 0) or 1 (a = 0).
+- A doubling map shifted by half a voxel, labels: every covered voxel's
+  mapped x is a half-integer, the exact tie goes to the even neighbour, and
+  both neighbours are allowed.
 - Soundness: per tet and side, the oracle's sum equals the exact-decision
   sum computed here in rationals (Fraction), and an FP32 evaluation of T(p)
   and of the sample (numpy, no fused operations) changes the case of h only
@@ -82,55 +83,69 @@ def _inner_box(nx, ny, nz, cells=(2, 2, 2)):
 
 
 @pytest.mark.parametrize("t", [(1, 0, 0), (0, -1, 1), (0, 0, 0)])
-def test_integer_translation_closed_form(oracle_lib, t):
+def test_integer_translation_is_exact(oracle_lib, t):
+    """A translation by whole voxels has map rows in {-1, 0, 1}: FP32
+    evaluates it exactly, so the report leaves nothing open, and the labels
+    are those at p + t."""
     nz, ny, nx = 8, 9, 10
     img_s, img_t = _two_level((nz, ny, nx), 4), _two_level((nz, ny, nx), 5)
     pts, tets = _inner_box(nx, ny, nz)
     tgt = (pts + np.array(t, np.float32)).astype(np.float32)
-    prob = problem(img_s, img_t, pts, tets, h_mode=1, g_mode=2)
-    o = oracle.Oracle(prob)
+    o = oracle.Oracle(problem(img_s, img_t, pts, tets, h_mode=1, g_mode=2))
     o.set_perturbation(GAMMA_POS, GAMMA_VAL)
     r = o.eval(pts, tgt, with_tets=True)
-    # side 0: the covered source voxels p (indices 2 .. n - 3) sample the
-    # target image at the grid point p + t
+    assert (r["tets"]["amb_n"] == 0).all() and (r["tets"]["amb_slack"] == 0).all()
     k, j, i = np.meshgrid(np.arange(2, nz - 2), np.arange(2, ny - 2), np.arange(2, nx - 2), indexing="ij")
-    yi, yj, yk = i + t[0], j + t[1], k + t[2]
+    lab = (np.arange(nx * ny * nz, dtype=np.int64).reshape(nz, ny, nx) % 7).astype(np.uint8)
+    w, cand = o.warp_labels(pts, tgt, 0, lab, candidates=True)
+    np.testing.assert_array_equal(w[k, j, i], lab[k + t[2], j + t[1], i + t[0]])
+    assert (cand == w[..., None]).all()
+
+
+def test_doubling_map_closed_form(oracle_lib):
+    """T(p) = 2 p (entries 2: not exact by the rule, so eps > 0): every
+    mapped position is a grid point, the sample is the stored value there,
+    and a voxel is open exactly when that value is 0 and a nonzero value
+    lies in the 3x3x3 neighbourhood; the spread is |a^2 - 1| (a > 0) or 1
+    (a = 0)."""
+    n = 16
+    img_s, img_t = _two_level((n, n, n), 4), _two_level((n, n, n), 5)
+    pts, tets = box_lattice(*([np.linspace(1.5, 5.5, 3)] * 3))
+    tgt = (2.0 * pts).astype(np.float32)
+    o = oracle.Oracle(problem(img_s, img_t, pts, tets, h_mode=1, g_mode=2))
+    o.set_perturbation(GAMMA_POS, GAMMA_VAL)
+    r = o.eval(pts, tgt, with_tets=True)
+    k, j, i = np.meshgrid(*([np.arange(2, 6)] * 3), indexing="ij")     # covered source voxels
     assert r["tets"]["n_vox"][:, 0].sum() == i.size
-    b = img_t[yk, yj, yi].astype(np.float64)
-    nonzero_near = ndimage.maximum_filter((img_t != 0).astype(np.uint8), size=3, mode="constant")[yk, yj, yi] > 0
-    amb = (b == 0) & nonzero_near
+    b = img_t[2 * k, 2 * j, 2 * i].astype(np.float64)
+    near = ndimage.maximum_filter((img_t != 0).astype(np.uint8), size=3, mode="constant")[2 * k, 2 * j, 2 * i] > 0
+    amb = (b == 0) & near
     a = img_s[k, j, i].astype(np.float64)
     spread = np.where(a > 0, np.abs(a * a - 1.0), np.where(a == 0, 1.0, 0.0))
     assert amb.sum() > 0
     assert r["tets"]["amb_n"][:, 0].sum() == amb.sum()
     assert r["tets"]["amb_slack"][:, 0].sum() == pytest.approx(spread[amb].sum(), rel=1e-12)
-    # and the returned sum is the exact-decision one
     h = np.where((a > 0) & (b > 0), (a - b) ** 2, np.where((a == 0) & (b == 0), 0.0, 1.0))
     assert r["tets"]["e_img"][:, 0].sum() == pytest.approx(h.sum(), rel=1e-12)
-    # labels: an integer translation fixes every voxel's nearest voxel
-    lab = (np.arange(nx * ny * nz, dtype=np.int64).reshape(nz, ny, nx) % 7).astype(np.uint8)
-    w, cand = o.warp_labels(pts, tgt, 0, lab, candidates=True)
-    np.testing.assert_array_equal(w[k, j, i], lab[yk, yj, yi])
-    assert (cand == w[..., None]).all()
 
 
-def test_half_voxel_translation_labels(oracle_lib):
-    nz, ny, nx = 7, 7, 12
-    img = _two_level((nz, ny, nx), 6)
-    pts, tets = _inner_box(nx, ny, nz)
-    tgt = (pts + np.array([0.5, 0.0, 0.0], np.float32)).astype(np.float32)
+def test_half_voxel_labels_closed_form(oracle_lib):
+    """T(p) = 2 p + (1/2, 0, 0): x lands exactly on half-integers, where the
+    exact tie goes to the even neighbour 2x and the report allows both 2x
+    and 2x + 1; y and z land on grid points and stay fixed."""
+    n = 16
+    img = _two_level((n, n, n), 6)
+    pts, tets = box_lattice(*([np.linspace(1.5, 5.5, 3)] * 3))
+    tgt = (2.0 * pts + np.array([0.5, 0.0, 0.0])).astype(np.float32)
     o = oracle.Oracle(problem(img, img, pts, tets, g_mode=2))
     o.set_perturbation(GAMMA_POS, GAMMA_VAL)
-    lab = np.random.default_rng(7).integers(0, 9, size=(nz, ny, nx)).astype(np.uint8)
+    lab = np.random.default_rng(7).integers(0, 9, size=(n, n, n)).astype(np.uint8)
     w, cand = o.warp_labels(pts, tgt, 0, lab, candidates=True)
-    sl = (slice(2, nz - 2), slice(2, ny - 2))
-    for x in range(2, nx - 2):
-        # T(p).x = x + 1/2: round half to even takes x (x even) or x + 1 (x odd);
-        # the two neighbours are the candidates (slot bit 0 = the x choice)
-        assert (w[sl + (x,)] == lab[sl + (x + (x % 2),)]).all()
-        c = cand[sl + (x,)]
-        assert (c[..., 0::2] == lab[sl + (x,)][..., None]).all()
-        assert (c[..., 1::2] == lab[sl + (x + 1,)][..., None]).all()
+    k, j, i = np.meshgrid(*([np.arange(2, 6)] * 3), indexing="ij")
+    np.testing.assert_array_equal(w[k, j, i], lab[2 * k, 2 * j, 2 * i])
+    c = cand[k, j, i]                                  # slot bit 0 = the x choice
+    assert (c[..., 0::2] == lab[2 * k, 2 * j, 2 * i][..., None]).all()
+    assert (c[..., 1::2] == lab[2 * k, 2 * j, 2 * i + 1][..., None]).all()
     assert (w[:, :, :2] == 255).all() and (cand[:, :, :2] == 255).all()     # not covered
 
 
