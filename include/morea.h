@@ -127,6 +127,13 @@ typedef struct morea_problem_desc {
     int32_t max_changed;           /* largest changed-point count of one request (0: 64) */
     int32_t estimator;             /* morea_estimator (0: VOXELS) */
     float sampling_rate;           /* SAMPLED: points per voxel^3 of tet volume (<= 0: 1.0) */
+    const uint8_t *tissue_mask;    /* host [nz][ny][nx] tissue label of each voxel of I_s, or NULL.
+                                    * Given (with tissue_factor, labels < n_labels <= 64), the
+                                    * elasticity factor of a tet is the mean of tissue_factor over
+                                    * the labels of the voxel centres in its reference copy (exact
+                                    * association): sum_k frac_k f_k + (1 - sum_k frac_k) f_0 with
+                                    * label 0 the background (App. A.1).  A tet that contains no
+                                    * voxel centre keeps tissue_factor[tet_label]. */
 } morea_problem_desc;
 
 /* Per-(slot, tet) summands kept by the handle (what a partial evaluation

@@ -45,7 +45,7 @@ class _Problem(ctypes.Structure):
         ("trunc_radius", ctypes.c_double),
         ("h_mode", ctypes.c_int32), ("g_mode", ctypes.c_int32),
         ("subvoxel_bits", ctypes.c_int32), ("estimator", ctypes.c_int32),
-        ("sampling_rate", ctypes.c_double),
+        ("sampling_rate", ctypes.c_double), ("tissue_mask", ctypes.c_void_p),
     ]
 
 
@@ -130,6 +130,8 @@ def lib():
                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                               ctypes.c_void_p]
         L.orc_set_perturbation.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double]
+        L.orc_cdelta.argtypes = [ctypes.c_void_p]
+        L.orc_cdelta.restype = ctypes.c_void_p
         L.orc_dvf.restype = ctypes.c_int
         L.orc_gexp.argtypes = [ctypes.c_double]
         L.orc_gexp.restype = ctypes.c_double
@@ -194,7 +196,8 @@ class Oracle:
                      trunc_radius=float(g("trunc_radius")), h_mode=int(g("h_mode")),
                      g_mode=int(g("g_mode")), subvoxel_bits=int(g("subvoxel_bits")),
                      estimator=int(getattr_default(g, "estimator", 0)),
-                     sampling_rate=float(np.float32(getattr_default(g, "sampling_rate", 1.0))))
+                     sampling_rate=float(np.float32(getattr_default(g, "sampling_rate", 1.0))),
+                     tissue_mask=_ptr(arr(getattr_default(g, "tissue_mask", None), np.uint8)))
         self._P = P
         self.nx, self.ny, self.nz = nx, ny, nz
         self.n_points = int(ref.shape[0])
@@ -225,6 +228,11 @@ class Oracle:
         p = self._L.orc_oriented_tets(self._h)
         return np.ctypeslib.as_array(ctypes.cast(p, ctypes.POINTER(ctypes.c_int32)),
                                      shape=(self.n_tets, 4)).copy()
+
+    def cdelta(self) -> np.ndarray:
+        """Elasticity factor c_delta of every tet (App. A.1)."""
+        p = self._L.orc_cdelta(self._h)
+        return np.ctypeslib.as_array(ctypes.cast(p, ctypes.POINTER(ctypes.c_double)), shape=(self.n_tets,)).copy()
 
     def distance_map(self, side: int, group: int) -> np.ndarray:
         p = self._L.orc_distance(self._h, side, group)

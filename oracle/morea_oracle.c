@@ -156,6 +156,7 @@ typedef struct {
     double trunc_radius;            /* <= 0: 2.5% of nx */
     int32_t h_mode, g_mode, subvoxel_bits, estimator;   /* estimator: 0 voxels (R3), 1 samples (R13) */
     double sampling_rate;           /* R13: points per voxel^3 (the float value given) */
+    const uint8_t *tissue_mask;     /* [nz][ny][nx] tissue label per voxel of I_s, or NULL (App. A.1) */
 } orc_problem;
 
 typedef struct {
@@ -896,6 +897,50 @@ void orc_free(orc_state *st)
     free(st);
 }
 
+/* App. A.1, elasticity from tissue overlap: c = sum_k frac_k f_k +
+ * (1 - sum_k frac_k) f_0 with label 0 the background.  frac_k is taken on
+ * the voxel grid: the voxel centres of the tet's (positively oriented)
+ * reference copy by the association of R3, counted per label of the mask;
+ * then c = sum_l count_l f_l / sum_l count_l, in label order.  A tet with
+ * no voxel centre keeps the factor of its label. */
+static void tissue_factor_of(orc_state *st, int t)
+{
+    const orc_problem *P = &st->p;
+    int64_t count[64];
+    memset(count, 0, sizeof(count));
+    orc_i3 v[4];
+    for (int i = 0; i < 4; ++i) v[i] = snap3(st, P->ref_points + 3 * (size_t)st->tets[4 * t + i]);
+    int64_t S = st->S, H = st->S / 2;
+    int n[3] = {P->nx, P->ny, P->nz};
+    int64_t lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) {
+        int64_t mn = INT64_MAX, mx = INT64_MIN;
+        for (int i = 0; i < 4; ++i) {
+            int64_t c = a == 0 ? v[i].x : a == 1 ? v[i].y : v[i].z;
+            if (c < mn) mn = c;
+            if (c > mx) mx = c;
+        }
+        lo[a] = ceil_div(mn - H, S);
+        hi[a] = floor_div(mx - H, S);
+        if (lo[a] < 0) lo[a] = 0;
+        if (hi[a] > n[a] - 1) hi[a] = n[a] - 1;
+    }
+    for (int64_t k = lo[2]; k <= hi[2]; ++k)
+        for (int64_t j = lo[1]; j <= hi[1]; ++j)
+            for (int64_t i = lo[0]; i <= hi[0]; ++i) {
+                orc_i3 p = {i * S + H, j * S + H, k * S + H};
+                if (!inside_sos(v, p)) continue;
+                count[P->tissue_mask[((size_t)k * P->ny + (size_t)j) * P->nx + (size_t)i]] += 1;
+            }
+    int64_t total = 0;
+    double s = 0.0;
+    for (int l = 0; l < P->n_labels; ++l) {
+        total += count[l];
+        s += (double)count[l] * P->tissue_factor[l];
+    }
+    if (total > 0) st->cdelta[t] = s / (double)total;
+}
+
 /* R7: brute-force Euclidean distance map of one contour point set. */
 static void distance_map(const orc_problem *P, const float *pts, int g, double *out)
 {
@@ -960,6 +1005,13 @@ int orc_setup(const orc_problem *P, orc_state **out)
             st->cdelta[t] = 1.0;
         }
     }
+    if (P->tissue_mask) {
+        if (!P->tissue_factor || P->n_labels > 64) { orc_free(st); return ORC_EINVAL; }
+        size_t N = (size_t)P->nx * P->ny * P->nz;
+        for (size_t v = 0; v < N; ++v)
+            if (P->tissue_mask[v] >= P->n_labels) { orc_free(st); return ORC_EINVAL; }
+        for (int t = 0; t < P->n_tets; ++t) tissue_factor_of(st, t);
+    }
     /* guidance groups, weights |C^k| / |G| and truncation radius */
     st->G = 0;
     for (int m = 0; m < P->n_guid; ++m) {
@@ -997,6 +1049,7 @@ void orc_set_perturbation(orc_state *st, double gamma_pos, double gamma_val)
 int orc_n_groups(const orc_state *st) { return st->G; }
 double orc_radius(const orc_state *st) { return st->r; }
 const int32_t *orc_oriented_tets(const orc_state *st) { return st->tets; }
+const double *orc_cdelta(const orc_state *st) { return st->cdelta; }
 const double *orc_distance(const orc_state *st, int side, int g)
 {
     if (!st->dist[side] || g < 0 || g >= st->G) return NULL;

@@ -135,11 +135,15 @@ morea_status morea_create_problem(const morea_problem_desc *d, void *stream, mor
     if (d->max_solutions < 1 || d->max_requests < 0 || d->max_changed < 0 || d->max_changed > 1024)
         return MOREA_EINVAL;
     if (d->tissue_factor && d->n_labels < 1) return MOREA_EINVAL;
+    if (d->tissue_mask && (!d->tissue_factor || d->n_labels > kMaxTissueLabels)) return MOREA_EINVAL;
     const int nx = d->nx, ny = d->ny, nz = d->nz;
     const long long N = (long long)nx * ny * nz;
     const int V = d->n_points, T = d->n_tets;
     const int k = choose_subvoxel_bits(d->subvoxel_bits, nx, ny, nz, T);
     if (k < 0) return MOREA_EINVAL;
+    if (d->tissue_mask)
+        for (long long v = 0; v < N; ++v)
+            if (d->tissue_mask[v] >= d->n_labels) return MOREA_EINVAL;
     int G = 0;
     for (int m = 0; m < d->n_guid; ++m) {
         const int g = d->guid_group ? d->guid_group[m] : 0;
@@ -377,6 +381,27 @@ morea_status morea_create_problem(const morea_problem_desc *d, void *stream, mor
     TRY(cudaMemcpyAsync(img[1], d->image_t, (size_t)N * esz, cudaMemcpyDefault, st));
     TRY(cudaMemcpyAsync(dtets, tets.data(), sizeof(int4) * T, cudaMemcpyHostToDevice, st));
     TRY(cudaMemcpyAsync(dcd, cdelta.data(), sizeof(float) * T, cudaMemcpyHostToDevice, st));
+    if (d->tissue_mask) {
+        // elasticity from mask overlap (App. A.1): staged inputs, freed before returning
+        std::vector<int4> q4(V);
+        for (int v = 0; v < V; ++v) q4[v] = make_int4(qref[3 * v], qref[3 * v + 1], qref[3 * v + 2], 0);
+        uint8_t *dmask = nullptr;
+        int4 *dq = nullptr;
+        double *dfac = nullptr;
+        cudaError_t e = cudaMalloc(&dmask, (size_t)N);
+        if (e == cudaSuccess) e = cudaMalloc(&dq, sizeof(int4) * V);
+        if (e == cudaSuccess) e = cudaMalloc(&dfac, sizeof(double) * d->n_labels);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dmask, d->tissue_mask, (size_t)N, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dq, q4.data(), sizeof(int4) * V, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dfac, d->tissue_factor, sizeof(double) * d->n_labels, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = launch_tissue_factors(hp, dtets, dq, dmask, dfac, d->n_labels, dcd, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        cudaFree(dmask);
+        cudaFree(dq);
+        cudaFree(dfac);
+        TRY(e);
+    }
     TRY(cudaMemcpyAsync(p->v2t_off, v2t_off.data(), sizeof(int) * (V + 1), cudaMemcpyHostToDevice, st));
     if (!v2t_idx.empty())
         TRY(cudaMemcpyAsync(p->v2t_idx, v2t_idx.data(), sizeof(int) * v2t_idx.size(), cudaMemcpyHostToDevice, st));

@@ -175,6 +175,12 @@ cudaError_t launch_init(const DevProblem *dp, const DevProblem &hp, int n_sol, f
                         const uint8_t *fixed, int n_kernels, const float *kernels, int max_rounds, int *rounds,
                         cudaStream_t st);
 int dvf_max_labels();
+// Elasticity factors from a tissue mask (k_tissue.cu): per tet, the mean of
+// factor[mask] over the voxel centres of its positively oriented reference
+// copy; tets with no voxel centre keep their value in cdelta.
+constexpr int kMaxTissueLabels = 64;
+cudaError_t launch_tissue_factors(const DevProblem &hp, const int4 *tets, const int4 *qref, const uint8_t *mask,
+                                  const double *factor, int n_labels, float *cdelta, cudaStream_t st);
 cudaError_t launch_dvf(const DevProblem *dp, const DevProblem &hp, const float *src, const float *tgt, int side,
                        float *dvf, const uint8_t *lab_own, const uint8_t *lab_oth, int n_labels,
                        unsigned long long *counts, uint8_t *warped, cudaStream_t st);

@@ -76,6 +76,7 @@ class ProblemDesc(ctypes.Structure):
         ("subvoxel_bits", ctypes.c_int32), ("max_solutions", ctypes.c_int32),
         ("max_requests", ctypes.c_int32), ("max_changed", ctypes.c_int32),
         ("estimator", ctypes.c_int32), ("sampling_rate", ctypes.c_float),
+        ("tissue_mask", ctypes.c_void_p),
     ]
 
 
@@ -306,7 +307,8 @@ class Problem:
             trunc_radius=float(g("trunc_radius")), h_mode=int(g("h_mode")), g_mode=int(g("g_mode")),
             subvoxel_bits=int(g("subvoxel_bits")), max_solutions=int(max_solutions),
             max_requests=int(max_requests), max_changed=int(max_changed),
-            estimator=int(g_opt("estimator", 0)), sampling_rate=float(g_opt("sampling_rate", 1.0)))
+            estimator=int(g_opt("estimator", 0)), sampling_rate=float(g_opt("sampling_rate", 1.0)),
+            tissue_mask=ptr(host(g_opt("tissue_mask", None), np.uint8)))
         h = ctypes.c_void_p()
         _check(L.morea_create_problem(ctypes.byref(desc), _stream(stream), ctypes.byref(h)),
                "morea_create_problem")

@@ -60,7 +60,7 @@ int main(void) {
   P(morea_problem_desc, image_s) P(morea_problem_desc, n_points) P(morea_problem_desc, tets)
   P(morea_problem_desc, n_labels) P(morea_problem_desc, guid_s) P(morea_problem_desc, trunc_radius)
   P(morea_problem_desc, h_mode) P(morea_problem_desc, max_changed)
-  P(morea_problem_desc, estimator) P(morea_problem_desc, sampling_rate)
+  P(morea_problem_desc, estimator) P(morea_problem_desc, sampling_rate) P(morea_problem_desc, tissue_mask)
   P(morea_tet_record, n_vox) P(morea_tet_record, e_mag) P(morea_tet_record, sev)
   P(morea_totals, n_vox) P(morea_totals, sev)
   return 0;
@@ -117,6 +117,19 @@ def test_invalid_descriptions_rejected_on_host(mo, bad):
     rc = mo.lib().morea_create_problem(ctypes.byref(d), None, ctypes.byref(h))
     assert rc == mo.EINVAL
     assert not h.value
+
+
+def test_tissue_mask_checked_on_host(mo):
+    """A tissue mask needs tissue factors, at most 64 labels and every voxel
+    label below n_labels; each violation is rejected before any device work."""
+    bad_label = np.zeros((32, 32, 32), np.uint8)
+    bad_label[3, 4, 5] = 4                     # n_labels is 4
+    ok = np.zeros((32, 32, 32), np.uint8)
+    for mask, kw in ((bad_label, {}), (ok, dict(tissue_factor=None)), (ok, dict(n_labels=65))):
+        d, keep = _desc(mo, tissue_mask=mask.ctypes.data_as(ctypes.c_void_p), **kw)
+        h = ctypes.c_void_p(123)
+        assert mo.lib().morea_create_problem(ctypes.byref(d), None, ctypes.byref(h)) == mo.EINVAL
+        assert not h.value
 
 
 def test_degenerate_or_out_of_range_topology_rejected(mo):
