@@ -18,6 +18,8 @@
 // 16- or 8-byte load per z-plane of the other image's 2x2x2 neighbourhood
 // from its "quad" copy, and the band mask only in rows that touch a guidance
 // band.
+#include <algorithm>
+
 #include "image_ops.cuh"
 
 namespace morea {
@@ -119,13 +121,13 @@ struct RowQueue {
 };
 
 // Image pass (a4, a5, a7): one warp per (entry, side).
-template <typename TI, int HMODE, int PASS>
+template <typename TI, int HMODE, int PASS, bool ORDERED>
 __global__ void __launch_bounds__(kBlock, 6) k_raster(const DevProblem *__restrict__ probs,
                                                      const WorkEntry *__restrict__ entries,
                                                      const RasterSetup *__restrict__ setup,
                                                      RasterOut *__restrict__ rout, int2 *__restrict__ bandrows,
                                                      const int *n_entries_dev, int n_entries_host, int chunk,
-                                                     int *queue)
+                                                     int *queue, const int *order)
 {
     using QT = typename QuadOf<TI>::T;
     __shared__ RowQueue rowq[kBlock / 32];
@@ -135,8 +137,9 @@ __global__ void __launch_bounds__(kBlock, 6) k_raster(const DevProblem *__restri
     RowQueue &Q = rowq[threadIdx.x >> 5];
     const int n_ent = n_entries_dev ? min(*n_entries_dev, n_entries_host) : n_entries_host;
     const int n_items = 2 * n_ent;
-    run_items(n_items, chunk, queue + kQueueRaster, [&](const int item) {
-        const int side = item >= n_ent ? 1 : 0;      // all source sides first, then all target sides
+    run_items(n_items, chunk, queue + kQueueRaster, [&](const int qi) {
+        const int item = ORDERED ? order[qi] : qi;    // the entry pass's order (largest copies first)
+        const int side = item >= n_ent ? 1 : 0;      // all source sides, then all target sides
         const int e = item - side * n_ent;
         const RasterSetup *su = setup + 2 * (size_t)e + side;
         const unsigned char *sb = reinterpret_cast<const unsigned char *>(su);
@@ -442,54 +445,71 @@ __global__ void __launch_bounds__(kBlock, 4) k_guidance(const DevProblem *__rest
     });
 }
 
-template <typename TI, int HMODE>
+template <typename TI, int HMODE, bool ORDERED>
 cudaError_t launch_g(const DevProblem *probs, int g_mode, const WorkEntry *entries, const RasterSetup *setup,
                      RasterOut *rout, int2 *bandrows, const int *n_dev, int n_host, int grid, int chunk, int *queue,
-                     cudaStream_t st)
+                     const int *order, cudaStream_t st)
 {
     switch (g_mode) {
     case MOREA_G_CONTINUOUS:
-        k_raster<TI, HMODE, kPassImageBand><<<grid, kBlock, 0, st>>>(probs, entries, setup, rout, bandrows, n_dev,
-                                                                    n_host, chunk, queue);
+        k_raster<TI, HMODE, kPassImageBand, ORDERED><<<grid, kBlock, 0, st>>>(probs, entries, setup, rout, bandrows,
+                                                                             n_dev, n_host, chunk, queue, order);
         if (cudaPeekAtLastError() == cudaSuccess)
             k_guidance<<<grid, kBlock, 0, st>>>(probs, entries, setup, rout, bandrows, n_dev, n_host, chunk,
                                                 queue);
         break;
     case MOREA_G_PAIR_TRANSFER:
-        k_raster<TI, HMODE, kPassImagePairs><<<grid, kBlock, 0, st>>>(probs, entries, setup, rout, bandrows, n_dev,
-                                                                     n_host, chunk, queue);
+        k_raster<TI, HMODE, kPassImagePairs, ORDERED><<<grid, kBlock, 0, st>>>(probs, entries, setup, rout,
+                                                                              bandrows, n_dev, n_host, chunk, queue,
+                                                                              order);
         break;
     default:
-        k_raster<TI, HMODE, kPassImage><<<grid, kBlock, 0, st>>>(probs, entries, setup, rout, bandrows, n_dev,
-                                                                n_host, chunk, queue);
+        k_raster<TI, HMODE, kPassImage, ORDERED><<<grid, kBlock, 0, st>>>(probs, entries, setup, rout, bandrows,
+                                                                         n_dev, n_host, chunk, queue, order);
         break;
     }
     return cudaGetLastError();
+}
+
+// Kernel variant of a launch: storage type, h mode and whether the items
+// come in the entry pass's order.
+template <typename TI, int HMODE>
+cudaError_t launch_o(const DevProblem *probs, int g_mode, const WorkEntry *entries, const RasterSetup *setup,
+                     RasterOut *rout, int2 *bandrows, const int *n_dev, int n_host, int grid, int chunk, int *queue,
+                     const int *order, cudaStream_t st)
+{
+    if (order)
+        return launch_g<TI, HMODE, true>(probs, g_mode, entries, setup, rout, bandrows, n_dev, n_host, grid, chunk,
+                                         queue, order, st);
+    return launch_g<TI, HMODE, false>(probs, g_mode, entries, setup, rout, bandrows, n_dev, n_host, grid, chunk,
+                                      queue, nullptr, st);
 }
 
 }  // namespace
 
 cudaError_t launch_raster(const DevProblem *probs, const DevProblem &hp, const WorkEntry *entries,
                           const RasterSetup *setup, RasterOut *rout, int2 *bandrows, const int *n_entries_dev,
-                          int n_entries_host, int grid, int chunk, int *queue, cudaStream_t st)
+                          int n_entries_host, int grid, int chunk, int *queue, bool ordered, cudaStream_t st)
 {
+    const int *order = ordered ? queue + kQueueList + 2 * (size_t)n_entries_host : nullptr;
     if (grid <= 0) grid = sm_count() * 8;
     cudaError_t e = cudaMemsetAsync(queue, 0, kQueueList * sizeof(int), st);
     if (e != cudaSuccess) return e;
+
     if (hp.estimator == MOREA_EST_SAMPLED)
         return launch_sample(probs, hp, entries, setup, rout, n_entries_dev, n_entries_host, grid, chunk, queue, st);
     if (hp.dtype == MOREA_F16) {
         if (hp.h_mode == MOREA_H_MOREA_FG)
-            return launch_g<__half, MOREA_H_MOREA_FG>(probs, hp.g_mode, entries, setup, rout, bandrows, n_entries_dev,
-                                                      n_entries_host, grid, chunk, queue, st);
-        return launch_g<__half, MOREA_H_PLAIN_SSD>(probs, hp.g_mode, entries, setup, rout, bandrows, n_entries_dev,
-                                                   n_entries_host, grid, chunk, queue, st);
+            return launch_o<__half, MOREA_H_MOREA_FG>(probs, hp.g_mode, entries, setup, rout, bandrows, n_entries_dev,
+                                                      n_entries_host, grid, chunk, queue, order, st);
+        return launch_o<__half, MOREA_H_PLAIN_SSD>(probs, hp.g_mode, entries, setup, rout, bandrows, n_entries_dev,
+                                                   n_entries_host, grid, chunk, queue, order, st);
     }
     if (hp.h_mode == MOREA_H_MOREA_FG)
-        return launch_g<float, MOREA_H_MOREA_FG>(probs, hp.g_mode, entries, setup, rout, bandrows, n_entries_dev,
-                                                 n_entries_host, grid, chunk, queue, st);
-    return launch_g<float, MOREA_H_PLAIN_SSD>(probs, hp.g_mode, entries, setup, rout, bandrows, n_entries_dev,
-                                              n_entries_host, grid, chunk, queue, st);
+        return launch_o<float, MOREA_H_MOREA_FG>(probs, hp.g_mode, entries, setup, rout, bandrows, n_entries_dev,
+                                                 n_entries_host, grid, chunk, queue, order, st);
+    return launch_o<float, MOREA_H_PLAIN_SSD>(probs, hp.g_mode, entries, setup, rout, bandrows, n_entries_dev,
+                                              n_entries_host, grid, chunk, queue, order, st);
 }
 
 }  // namespace morea

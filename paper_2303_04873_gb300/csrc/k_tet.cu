@@ -44,9 +44,16 @@ __global__ void __launch_bounds__(kBlock) k_snap_slots(const DevProblem *__restr
 // Per-entry work of the tet pass: one thread per (entry, side) builds that
 // copy's rasterisation set-up; the side-0 thread also evaluates the fold and
 // magnitude terms of the tet.
+// With rqueue, every item (entry, side) also takes a place in the image
+// pass's order: copies whose bounding box holds at least kBigItemVoxels
+// voxel centres from the front, the others from the back, so the pass does
+// not end waiting on a few large copies taken late (longest first).
+// Within each group the order is arbitrary; an item's result does not
+// depend on when it runs.
 __global__ void __launch_bounds__(kBlock) k_entry_work(const DevProblem *__restrict__ probs,
                                                       const WorkEntry *__restrict__ entries, RasterSetup *setup,
-                                                      TetOut *tout, const int *n_entries_dev, int n_entries_host)
+                                                      TetOut *tout, const int *n_entries_dev, int n_entries_host,
+                                                      int *rqueue)
 {
     const int n_ent = n_entries_dev ? min(*n_entries_dev, n_entries_host) : n_entries_host;
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < 2LL * n_ent;
@@ -63,6 +70,15 @@ __global__ void __launch_bounds__(kBlock) k_entry_work(const DevProblem *__restr
         RasterSetup su;
         make_setup(own, oth, P, su);
         setup[g] = su;
+        if (rqueue) {
+            const long long vox = (su.valid & 1) ? (long long)max(su.ihi - su.ilo + 1, 0) *
+                                                       max(su.jhi - su.jlo + 1, 0) * max(su.khi - su.klo + 1, 0)
+                                                 : 0;
+            const int n_items = 2 * n_ent;
+            const int pos = vox >= kBigItemVoxels ? atomicAdd(rqueue + kQueueOrderBig, 1)
+                                                  : n_items - 1 - atomicAdd(rqueue + kQueueOrderSmall, 1);
+            rqueue[kQueueList + 2 * (size_t)n_entries_host + pos] = e + side * n_ent;   // raster item index
+        }
         if (side == 0) {
             TetOut to;
             tet_terms(own, oth, P, we.tet, to);
@@ -711,14 +727,14 @@ cudaError_t launch_full_entries(const DevProblem *dp, const DevProblem &hp, int 
     k_full_entries<<<grid_for((long long)n_sol * hp.n_tets), kBlock, 0, st>>>(dp, n_sol, slot, entries);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return launch_entry_work(dp, entries, setup, tout, nullptr, n_sol * hp.n_tets, st);
+    return launch_entry_work(dp, entries, setup, tout, nullptr, n_sol * hp.n_tets, nullptr, st);
 }
 
 cudaError_t launch_entry_work(const DevProblem *dp, const WorkEntry *entries, RasterSetup *setup, TetOut *tout,
-                              const int *n_entries_dev, int n_entries_host, cudaStream_t st)
+                              const int *n_entries_dev, int n_entries_host, int *rqueue, cudaStream_t st)
 {
     k_entry_work<<<grid_for(2LL * n_entries_host), kBlock, 0, st>>>(dp, entries, setup, tout, n_entries_dev,
-                                                                    n_entries_host);
+                                                                    n_entries_host, rqueue);
     return cudaGetLastError();
 }
 
@@ -758,7 +774,7 @@ cudaError_t launch_partial_entries(const DevProblem *dp, const DevProblem &hp, i
                                    const float *chg_tgt, int, int max_changed, const int *v2t_off,
                                    const int *v2t_idx, WorkEntry *entries, RasterSetup *setup,
                                    TetOut *tout, int cap_entries, int *counter, ReqInfo *rinfo,
-                                   int *req_chg_pts, int4 *req_chg_q, cudaStream_t st)
+                                   int *req_chg_pts, int4 *req_chg_q, int *rqueue, cudaStream_t st)
 {
     const size_t smem = partial_smem_bytes(hp.n_tets, max_changed);
     if (smem > 48 * 1024) {
@@ -771,7 +787,7 @@ cudaError_t launch_partial_entries(const DevProblem *dp, const DevProblem &hp, i
                                                    rinfo, req_chg_pts, req_chg_q);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return launch_entry_work(dp, entries, setup, tout, counter, cap_entries, st);
+    return launch_entry_work(dp, entries, setup, tout, counter, cap_entries, rqueue, st);
 }
 
 cudaError_t launch_partial_finalize(const DevProblem *dp, const DevProblem &, int n_req, const ReqInfo *rinfo,

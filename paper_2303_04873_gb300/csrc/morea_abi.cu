@@ -58,7 +58,7 @@ namespace {
 morea_status from_cuda(cudaError_t e) { return e == cudaSuccess ? MOREA_OK : MOREA_ECUDA; }
 
 // Rasterisation launch wrapped by the optional instrumentation.
-cudaError_t timed_raster(morea_problem *p, const int *n_dev, int n_host, int grid, cudaStream_t st)
+cudaError_t timed_raster(morea_problem *p, const int *n_dev, int n_host, int grid, bool ordered, cudaStream_t st)
 {
     cudaEvent_t a = nullptr, b = nullptr;
     if (p->prof & 1u) {
@@ -75,7 +75,7 @@ cudaError_t timed_raster(morea_problem *p, const int *n_dev, int n_host, int gri
         if (r != cudaSuccess) return r;
     }
     cudaError_t e = launch_raster(p->dp, p->hp, p->entries, p->setup, p->rout, p->bandrows, n_dev, n_host, grid,
-                                  p->launch.chunk, p->queue, st);
+                                  p->launch.chunk, p->queue, ordered, st);
     if (e == cudaSuccess && (p->prof & 1u)) e = cudaEventRecord(b, st);
     if (e == cudaSuccess && (p->prof & 2u)) e = launch_count_visits(p->rout, n_dev, n_host, p->visits, st);
     return e;
@@ -497,7 +497,7 @@ morea_status morea_eval_full(morea_problem *p, int32_t n_sol, const int32_t *slo
     if (e == cudaSuccess) {
         const long long items = 2LL * n_sol * p->T;
         const int grid = (int)std::min<long long>((long long)sm_count() * p->launch.blocks_per_sm, (items + 7) / 8);
-        e = timed_raster(p, nullptr, n_sol * p->T, grid, st);
+        e = timed_raster(p, nullptr, n_sol * p->T, grid, false, st);
     }
     if (e == cudaSuccess)
         e = launch_reduce_full(p->dp, p->hp, n_sol, slot, p->tout, p->rout, obj, folded, severity, st);
@@ -514,12 +514,15 @@ morea_status morea_eval_partial(morea_problem *p, int32_t n_req, const int32_t *
     DeviceGuard g(p->device);
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(p->counter, 0, sizeof(int), st);
+    // the entry pass orders the image pass's items (largest copies first): its counters start at zero
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->queue, 0, kQueueList * sizeof(int), st);
     if (e == cudaSuccess)
         e = launch_partial_entries(p->dp, p->hp, n_req, slot, chg_off, chg_pts, chg_src, chg_tgt, p->max_sol,
                                    p->max_changed, p->v2t_off, p->v2t_idx, p->entries, p->setup, p->tout,
-                                   p->cap_entries, p->counter, p->rinfo, p->req_chg_pts, p->req_chg_q, st);
+                                   p->cap_entries, p->counter, p->rinfo, p->req_chg_pts, p->req_chg_q, p->queue,
+                                   st);
     if (e == cudaSuccess)
-        e = timed_raster(p, p->counter, p->cap_entries, sm_count() * p->launch.blocks_per_sm, st);
+        e = timed_raster(p, p->counter, p->cap_entries, sm_count() * p->launch.blocks_per_sm, true, st);
     if (e == cudaSuccess)
         e = launch_partial_finalize(p->dp, p->hp, n_req, p->rinfo, p->entries, p->tout, p->rout, p->req_delta, obj,
                                     folded, severity, st);

@@ -78,12 +78,13 @@ cudaError_t enqueue_batch(morea_batch *b, const BatchTable &tb, cudaStream_t st)
     cudaError_t e = launch_batch_snap(b->dprobs, tb, st);
     if (e == cudaSuccess) e = launch_batch_entries(b->dprobs, tb, b->entries, st);
     if (e == cudaSuccess)
-        e = launch_entry_work(b->dprobs, b->entries, b->setup, b->tout, nullptr, (int)tb.total_entries, st);
+        e = launch_entry_work(b->dprobs, b->entries, b->setup, b->tout, nullptr, (int)tb.total_entries, nullptr,
+                              st);
     if (e == cudaSuccess) {
         const long long items = 2 * tb.total_entries;
         const int grid = (int)std::min<long long>((long long)sm_count() * b->launch.blocks_per_sm, (items + 7) / 8);
         e = launch_raster(b->dprobs, b->hp0, b->entries, b->setup, b->rout, b->bandrows, nullptr,
-                          (int)tb.total_entries, std::max(grid, 1), b->launch.chunk, b->queue, st);
+                          (int)tb.total_entries, std::max(grid, 1), b->launch.chunk, b->queue, false, st);
     }
     if (e == cudaSuccess) e = launch_batch_reduce(b->dprobs, tb, b->tout, b->rout, st);
     return e;

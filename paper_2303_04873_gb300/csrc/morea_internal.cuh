@@ -137,22 +137,33 @@ cudaError_t launch_snap_slots(const DevProblem *dp, const DevProblem &hp, int n_
                               cudaStream_t st);
 cudaError_t launch_full_entries(const DevProblem *dp, const DevProblem &hp, int n_sol, const int *slot,
                                 WorkEntry *entries, RasterSetup *setup, TetOut *tout, cudaStream_t st);
+// rqueue (or NULL): the image pass's queue; the entry pass then also writes
+// the order of its items (largest copies first, see kQueueList) and the
+// image pass takes the items in that order.
 cudaError_t launch_entry_work(const DevProblem *dp, const WorkEntry *entries, RasterSetup *setup, TetOut *tout,
-                              const int *n_entries_dev, int n_entries_host, cudaStream_t st);
+                              const int *n_entries_dev, int n_entries_host, int *rqueue, cudaStream_t st);
 cudaError_t launch_build_quads(const DevProblem &hp, int side, void *quad, cudaStream_t st);
 cudaError_t launch_band_rows(const DevProblem &hp, int side, short2 *bandrow, cudaStream_t st);
 // image pass (+ continuous guidance pass); bandrows: [2 * entries][kBandRowsPerItem] scratch
 constexpr int kBandRowsPerItem = 128;
 // chunk > 0 selects the atomic work queue.  queue: kQueueList device counters
-// (reset here) followed, in the continuous-guidance mode, by the list of the
-// (entry, side) items that have band rows (capacity 2 * n_entries_host).
+// (reset here), then the list of the (entry, side) items that have band rows
+// (continuous guidance; capacity 2 * n_entries_host), then the order in
+// which the image pass takes its items (2 * n_entries_host: the copies with
+// the largest bounding boxes first).
 constexpr int kQueueRaster = 0;      // work counter of the image pass
 constexpr int kQueueGuidance = 1;    // work counter of the guidance pass
 constexpr int kQueueListCount = 2;   // items listed for the guidance pass
-constexpr int kQueueList = 4;        // first list entry (16-byte aligned)
+constexpr int kQueueOrderBig = 3;    // large items placed in the order, from the front
+constexpr int kQueueOrderSmall = 4;  // the others, from the back
+constexpr int kQueueList = 8;        // first list entry (32-byte aligned)
+// A copy whose bounding box holds at least this many voxel centres is an
+// item the ordered image pass takes first.
+constexpr int kBigItemVoxels = 16384;
 inline size_t queue_ints(long long cap_entries, bool continuous)
 {
-    return kQueueList + (continuous ? 2 * (size_t)cap_entries : 0);
+    (void)continuous;
+    return kQueueList + 4 * (size_t)cap_entries;
 }
 // The sampled estimator (k_sample.cu): Sobol direction numbers into constant
 // memory (once per device), the dilated band masks, and the image pass.
@@ -190,7 +201,7 @@ cudaError_t launch_repair(const DevProblem *dp, const DevProblem &hp, const int 
                           int *moved, double *severity, cudaStream_t st);
 cudaError_t launch_raster(const DevProblem *probs, const DevProblem &hp, const WorkEntry *entries,
                           const RasterSetup *setup, RasterOut *rout, int2 *bandrows, const int *n_entries_dev,
-                          int n_entries_host, int grid, int chunk, int *queue, cudaStream_t st);
+                          int n_entries_host, int grid, int chunk, int *queue, bool ordered, cudaStream_t st);
 cudaError_t launch_reduce_full(const DevProblem *dp, const DevProblem &hp, int n_sol, const int *slot,
                                const TetOut *tout, const RasterOut *rout, double *obj, uint8_t *folded,
                                double *severity, cudaStream_t st);
@@ -199,7 +210,8 @@ cudaError_t launch_partial_entries(const DevProblem *dp, const DevProblem &hp, i
                                    const float *chg_tgt, int max_sol, int max_changed,
                                    const int *v2t_off, const int *v2t_idx, WorkEntry *entries,
                                    RasterSetup *setup, TetOut *tout, int cap_entries, int *counter,
-                                   ReqInfo *rinfo, int *req_chg_pts, int4 *req_chg_q, cudaStream_t st);
+                                   ReqInfo *rinfo, int *req_chg_pts, int4 *req_chg_q, int *rqueue,
+                                   cudaStream_t st);
 cudaError_t launch_partial_finalize(const DevProblem *dp, const DevProblem &hp, int n_req,
                                     const ReqInfo *rinfo, const WorkEntry *entries, const TetOut *tout,
                                     const RasterOut *rout, morea_totals *delta, double *obj,
