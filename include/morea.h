@@ -278,6 +278,17 @@ morea_status morea_batch_capture(morea_batch *b, const int32_t *n_sol, const flo
  * contents of the captured input buffers).  MOREA_EINVAL if none captured. */
 morea_status morea_batch_replay(morea_batch *b, void *stream);
 
+/* Per-problem completion times of the batch's last evaluation (direct or
+ * replayed), in ms after its first kernel started, measured on the device
+ * with %globaltimer (no events): records_ms[i] when the last image-pass or
+ * guidance item of problem i finished (its per-tet records are final),
+ * objectives_ms[i] when its last objective reduction finished.  Host arrays
+ * [n_problems], either may be NULL; -1 for a problem whose evaluation did
+ * not complete.  Synchronises the device.  The paper has no counterpart:
+ * it measures the batching of several registration problems in one launch
+ * sequence. */
+morea_status morea_batch_latency(morea_batch *b, double *records_ms, double *objectives_ms);
+
 /* Launch shape of the image and guidance passes, normally chosen by the
  * autotuner (paper_2303_04873_gb300.autotune): blocks_per_sm in [1, 64]
  * (grid = blocks_per_sm x SM count) and chunk in [0, 1024]: 0 = static

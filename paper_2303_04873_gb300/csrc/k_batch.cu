@@ -23,6 +23,16 @@ __device__ __forceinline__ int find_prob(const BatchTable &tb, long long g, Off 
 
 __global__ void __launch_bounds__(kBlock) k_batch_snap(const DevProblem *__restrict__ probs, const BatchTable tb)
 {
+    BatchClock *ck = probs[0].clock;
+    if (ck && blockIdx.x == 0 && threadIdx.x == 0) {
+        // completion clock of this evaluation: start time, item totals, counters cleared
+        ck->t0 = global_ns();
+        for (int i = 0; i < tb.n; ++i) {
+            ck->raster_total[i] = 2 * tb.p[i].n_sol * probs[i].n_tets;
+            ck->raster_done[i] = ck->guid_done[i] = ck->guid_total[i] = ck->reduce_done[i] = 0;
+            ck->t_raster[i] = ck->t_guid[i] = ck->t_reduce[i] = 0ull;
+        }
+    }
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < tb.total_verts;
          g += (long long)gridDim.x * blockDim.x) {
         const int pi = find_prob(tb, g, [](const BatchProb &b) { return b.vert_off; });
@@ -146,6 +156,11 @@ __global__ void __launch_bounds__(kBlock) k_batch_reduce(const DevProblem *__res
         if (bp.severity) {
             const double S = (double)P.S;
             bp.severity[i] = (double)sev / (6.0 * S * S * S);
+        }
+        BatchClock *ck = P.clock;
+        if (ck) {
+            __threadfence();                          // this solution's outputs before the stamp
+            if (atomicAdd(&ck->reduce_done[pi], 1) + 1 == bp.n_sol) ck->t_reduce[pi] = global_ns();
         }
     }
 }

@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(kBlock, 6) k_raster(const DevProblem *__restri
                                                      const RasterSetup *__restrict__ setup,
                                                      RasterOut *__restrict__ rout, int2 *__restrict__ bandrows,
                                                      const int *n_entries_dev, int n_entries_host, int chunk,
-                                                     int *queue, const int *order)
+                                                     int *queue, const int *order, BatchClock *clock)
 {
     using QT = typename QuadOf<TI>::T;
     __shared__ RowQueue rowq[kBlock / 32];
@@ -137,8 +137,11 @@ __global__ void __launch_bounds__(kBlock, 6) k_raster(const DevProblem *__restri
     RowQueue &Q = rowq[threadIdx.x >> 5];
     const int n_ent = n_entries_dev ? min(*n_entries_dev, n_entries_host) : n_entries_host;
     const int n_items = 2 * n_ent;
-    run_items(n_items, chunk, queue + kQueueRaster, [&](const int qi) {
-        const int item = ORDERED ? order[qi] : qi;    // the entry pass's order (largest copies first)
+    // ORDERED: the large items the entry pass listed first, then every item in
+    // its own order except those
+    const int n_big = ORDERED ? min(queue[kQueueOrderBig], n_items) : 0;
+    run_items(n_big + n_items, chunk, queue + kQueueRaster, [&](const int qi) {
+        const int item = qi < n_big ? order[qi] : qi - n_big;
         const int side = item >= n_ent ? 1 : 0;      // all source sides, then all target sides
         const int e = item - side * n_ent;
         const RasterSetup *su = setup + 2 * (size_t)e + side;
@@ -146,6 +149,10 @@ __global__ void __launch_bounds__(kBlock, 6) k_raster(const DevProblem *__restri
         const int4 bx = __ldg(reinterpret_cast<const int4 *>(sb + offsetof(RasterSetup, ilo)));
         const int2 bz2 = __ldg(reinterpret_cast<const int2 *>(sb + offsetof(RasterSetup, klo)));
         const int valid = __ldg(reinterpret_cast<const int *>(sb + offsetof(RasterSetup, valid)));
+        if (ORDERED && qi >= n_big && (valid & 1) &&
+            (long long)max(bx.y - bx.x + 1, 0) * max(bx.w - bx.z + 1, 0) * max(bz2.y - bz2.x + 1, 0) >=
+                kBigItemVoxels)
+            return;                                   // a large item, done from the list
         float s_img = 0.0f, c_img = 0.0f, s_g = 0.0f, c_g = 0.0f;
         int nvox = 0, ngp = 0;
         int nband = 0;                                // band rows recorded (warp-uniform)
@@ -321,6 +328,12 @@ __global__ void __launch_bounds__(kBlock, 6) k_raster(const DevProblem *__restri
             ro.n_gp = ngp;
             rout[2 * (size_t)e + side] = ro;
             if (PASS == kPassImageBand && nband > 0) queue[kQueueList + atomicAdd(queue + kQueueListCount, 1)] = item;
+            if (clock) {                              // batched evaluation: completion of the problem's items
+                const int pi = entries[e].prob;
+                if (PASS == kPassImageBand && nband > 0) atomicAdd(&clock->guid_total[pi], 1);
+                if (atomicAdd(&clock->raster_done[pi], 1) + 1 == clock->raster_total[pi])
+                    clock->t_raster[pi] = global_ns();
+            }
         }
     });
 }
@@ -441,6 +454,10 @@ __global__ void __launch_bounds__(kBlock, 4) k_guidance(const DevProblem *__rest
         if (lane == 0) {
             ro->e_guid = e_g;
             ro->n_gp = 0;
+            const int pi = entries[e].prob;
+            BatchClock *ck = P.clock;
+            // batched evaluation: the image pass counted this problem's listed items before this kernel began
+            if (ck && atomicAdd(&ck->guid_done[pi], 1) + 1 == ck->guid_total[pi]) ck->t_guid[pi] = global_ns();
         }
     });
 }
@@ -448,12 +465,12 @@ __global__ void __launch_bounds__(kBlock, 4) k_guidance(const DevProblem *__rest
 template <typename TI, int HMODE, bool ORDERED>
 cudaError_t launch_g(const DevProblem *probs, int g_mode, const WorkEntry *entries, const RasterSetup *setup,
                      RasterOut *rout, int2 *bandrows, const int *n_dev, int n_host, int grid, int chunk, int *queue,
-                     const int *order, cudaStream_t st)
+                     const int *order, BatchClock *clock, cudaStream_t st)
 {
     switch (g_mode) {
     case MOREA_G_CONTINUOUS:
         k_raster<TI, HMODE, kPassImageBand, ORDERED><<<grid, kBlock, 0, st>>>(probs, entries, setup, rout, bandrows,
-                                                                             n_dev, n_host, chunk, queue, order);
+                                                                             n_dev, n_host, chunk, queue, order, clock);
         if (cudaPeekAtLastError() == cudaSuccess)
             k_guidance<<<grid, kBlock, 0, st>>>(probs, entries, setup, rout, bandrows, n_dev, n_host, chunk,
                                                 queue);
@@ -461,11 +478,11 @@ cudaError_t launch_g(const DevProblem *probs, int g_mode, const WorkEntry *entri
     case MOREA_G_PAIR_TRANSFER:
         k_raster<TI, HMODE, kPassImagePairs, ORDERED><<<grid, kBlock, 0, st>>>(probs, entries, setup, rout,
                                                                               bandrows, n_dev, n_host, chunk, queue,
-                                                                              order);
+                                                                              order, clock);
         break;
     default:
         k_raster<TI, HMODE, kPassImage, ORDERED><<<grid, kBlock, 0, st>>>(probs, entries, setup, rout, bandrows,
-                                                                         n_dev, n_host, chunk, queue, order);
+                                                                         n_dev, n_host, chunk, queue, order, clock);
         break;
     }
     return cudaGetLastError();
@@ -476,24 +493,27 @@ cudaError_t launch_g(const DevProblem *probs, int g_mode, const WorkEntry *entri
 template <typename TI, int HMODE>
 cudaError_t launch_o(const DevProblem *probs, int g_mode, const WorkEntry *entries, const RasterSetup *setup,
                      RasterOut *rout, int2 *bandrows, const int *n_dev, int n_host, int grid, int chunk, int *queue,
-                     const int *order, cudaStream_t st)
+                     const int *order, BatchClock *clock, cudaStream_t st)
 {
     if (order)
         return launch_g<TI, HMODE, true>(probs, g_mode, entries, setup, rout, bandrows, n_dev, n_host, grid, chunk,
-                                         queue, order, st);
+                                         queue, order, clock, st);
     return launch_g<TI, HMODE, false>(probs, g_mode, entries, setup, rout, bandrows, n_dev, n_host, grid, chunk,
-                                      queue, nullptr, st);
+                                      queue, nullptr, clock, st);
 }
 
 }  // namespace
 
 cudaError_t launch_raster(const DevProblem *probs, const DevProblem &hp, const WorkEntry *entries,
                           const RasterSetup *setup, RasterOut *rout, int2 *bandrows, const int *n_entries_dev,
-                          int n_entries_host, int grid, int chunk, int *queue, bool ordered, cudaStream_t st)
+                          int n_entries_host, int grid, int chunk, int *queue, bool ordered, BatchClock *clock,
+                          cudaStream_t st)
 {
     const int *order = ordered ? queue + kQueueList + 2 * (size_t)n_entries_host : nullptr;
     if (grid <= 0) grid = sm_count() * 8;
-    cudaError_t e = cudaMemsetAsync(queue, 0, kQueueList * sizeof(int), st);
+    // the work counters and the guidance list; the large-item count of an
+    // ordered pass was set by the entry pass and stays
+    cudaError_t e = cudaMemsetAsync(queue, 0, kQueueOrderBig * sizeof(int), st);
     if (e != cudaSuccess) return e;
 
     if (hp.estimator == MOREA_EST_SAMPLED)
@@ -501,15 +521,15 @@ cudaError_t launch_raster(const DevProblem *probs, const DevProblem &hp, const W
     if (hp.dtype == MOREA_F16) {
         if (hp.h_mode == MOREA_H_MOREA_FG)
             return launch_o<__half, MOREA_H_MOREA_FG>(probs, hp.g_mode, entries, setup, rout, bandrows, n_entries_dev,
-                                                      n_entries_host, grid, chunk, queue, order, st);
+                                                      n_entries_host, grid, chunk, queue, order, clock, st);
         return launch_o<__half, MOREA_H_PLAIN_SSD>(probs, hp.g_mode, entries, setup, rout, bandrows, n_entries_dev,
-                                                   n_entries_host, grid, chunk, queue, order, st);
+                                                   n_entries_host, grid, chunk, queue, order, clock, st);
     }
     if (hp.h_mode == MOREA_H_MOREA_FG)
         return launch_o<float, MOREA_H_MOREA_FG>(probs, hp.g_mode, entries, setup, rout, bandrows, n_entries_dev,
-                                                 n_entries_host, grid, chunk, queue, order, st);
+                                                 n_entries_host, grid, chunk, queue, order, clock, st);
     return launch_o<float, MOREA_H_PLAIN_SSD>(probs, hp.g_mode, entries, setup, rout, bandrows, n_entries_dev,
-                                              n_entries_host, grid, chunk, queue, order, st);
+                                              n_entries_host, grid, chunk, queue, order, clock, st);
 }
 
 }  // namespace morea

@@ -169,6 +169,9 @@ __global__ void __launch_bounds__(kBlock, 4) k_sample(const DevProblem *__restri
             ro.n_vox = (int)n;
             ro.n_gp = 0;
             rout[2 * (size_t)e + side] = ro;
+            const int pi = entries[e].prob;
+            BatchClock *ck = probs[pi].clock;
+            if (ck && atomicAdd(&ck->raster_done[pi], 1) + 1 == ck->raster_total[pi]) ck->t_raster[pi] = global_ns();
         }
     });
 }

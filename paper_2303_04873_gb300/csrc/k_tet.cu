@@ -44,12 +44,11 @@ __global__ void __launch_bounds__(kBlock) k_snap_slots(const DevProblem *__restr
 // Per-entry work of the tet pass: one thread per (entry, side) builds that
 // copy's rasterisation set-up; the side-0 thread also evaluates the fold and
 // magnitude terms of the tet.
-// With rqueue, every item (entry, side) also takes a place in the image
-// pass's order: copies whose bounding box holds at least kBigItemVoxels
-// voxel centres from the front, the others from the back, so the pass does
-// not end waiting on a few large copies taken late (longest first).
-// Within each group the order is arbitrary; an item's result does not
-// depend on when it runs.
+// With rqueue, the items (entry, side) whose copy is large (item_is_big)
+// are also listed for the image pass, which takes them first and the rest
+// in their own order, so the pass does not end waiting on a few large
+// copies taken late.  The order of the list is arbitrary; an item's result
+// does not depend on when it runs.
 __global__ void __launch_bounds__(kBlock) k_entry_work(const DevProblem *__restrict__ probs,
                                                       const WorkEntry *__restrict__ entries, RasterSetup *setup,
                                                       TetOut *tout, const int *n_entries_dev, int n_entries_host,
@@ -70,13 +69,8 @@ __global__ void __launch_bounds__(kBlock) k_entry_work(const DevProblem *__restr
         RasterSetup su;
         make_setup(own, oth, P, su);
         setup[g] = su;
-        if (rqueue) {
-            const long long vox = (su.valid & 1) ? (long long)max(su.ihi - su.ilo + 1, 0) *
-                                                       max(su.jhi - su.jlo + 1, 0) * max(su.khi - su.klo + 1, 0)
-                                                 : 0;
-            const int n_items = 2 * n_ent;
-            const int pos = vox >= kBigItemVoxels ? atomicAdd(rqueue + kQueueOrderBig, 1)
-                                                  : n_items - 1 - atomicAdd(rqueue + kQueueOrderSmall, 1);
+        if (rqueue && item_is_big(su)) {
+            const int pos = atomicAdd(rqueue + kQueueOrderBig, 1);
             rqueue[kQueueList + 2 * (size_t)n_entries_host + pos] = e + side * n_ent;   // raster item index
         }
         if (side == 0) {

@@ -75,7 +75,7 @@ cudaError_t timed_raster(morea_problem *p, const int *n_dev, int n_host, int gri
         if (r != cudaSuccess) return r;
     }
     cudaError_t e = launch_raster(p->dp, p->hp, p->entries, p->setup, p->rout, p->bandrows, n_dev, n_host, grid,
-                                  p->launch.chunk, p->queue, ordered, st);
+                                  p->launch.chunk, p->queue, ordered, nullptr, st);
     if (e == cudaSuccess && (p->prof & 1u)) e = cudaEventRecord(b, st);
     if (e == cudaSuccess && (p->prof & 2u)) e = launch_count_visits(p->rout, n_dev, n_host, p->visits, st);
     return e;

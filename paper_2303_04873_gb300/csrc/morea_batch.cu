@@ -25,6 +25,7 @@ struct morea_batch {
     MoreaLaunch launch;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    BatchClock *clock = nullptr;          // completion clock of the last evaluation
 };
 
 namespace {
@@ -84,7 +85,8 @@ cudaError_t enqueue_batch(morea_batch *b, const BatchTable &tb, cudaStream_t st)
         const long long items = 2 * tb.total_entries;
         const int grid = (int)std::min<long long>((long long)sm_count() * b->launch.blocks_per_sm, (items + 7) / 8);
         e = launch_raster(b->dprobs, b->hp0, b->entries, b->setup, b->rout, b->bandrows, nullptr,
-                          (int)tb.total_entries, std::max(grid, 1), b->launch.chunk, b->queue, false, st);
+                          (int)tb.total_entries, std::max(grid, 1), b->launch.chunk, b->queue, false, b->clock,
+                          st);
     }
     if (e == cudaSuccess) e = launch_batch_reduce(b->dprobs, tb, b->tout, b->rout, st);
     return e;
@@ -133,9 +135,14 @@ morea_status morea_batch_create(morea_problem *const *problems, int32_t n_proble
     b->probs.assign(problems, problems + n_problems);
     b->hp0 = p0->hp;
     b->cap_entries = cap;
+    cudaError_t e = dalloc(b, &b->clock, 1);
     std::vector<DevProblem> hps(n_problems);
-    for (int i = 0; i < n_problems; ++i) hps[i] = problems[i]->hp;
-    cudaError_t e = dalloc(b, &b->dprobs, n_problems);
+    for (int i = 0; i < n_problems; ++i) {
+        hps[i] = problems[i]->hp;
+        hps[i].clock = b->clock;
+    }
+    if (e == cudaSuccess) e = cudaMemset(b->clock, 0, sizeof(BatchClock));
+    if (e == cudaSuccess) e = dalloc(b, &b->dprobs, n_problems);
     if (e == cudaSuccess) e = dalloc(b, &b->entries, (size_t)cap);
     if (e == cudaSuccess) e = dalloc(b, &b->setup, 2 * (size_t)cap);
     if (e == cudaSuccess) e = dalloc(b, &b->rout, 2 * (size_t)cap);
@@ -204,6 +211,24 @@ morea_status morea_batch_replay(morea_batch *b, void *stream)
     if (!b || !b->exec) return MOREA_EINVAL;
     DeviceGuard g(b->device);
     return from_cuda(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
+}
+
+morea_status morea_batch_latency(morea_batch *b, double *records_ms, double *objectives_ms)
+{
+    if (!b || (!records_ms && !objectives_ms)) return MOREA_EINVAL;
+    DeviceGuard g(b->device);
+    BatchClock ck;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&ck, b->clock, sizeof(ck), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return MOREA_ECUDA;
+    for (size_t i = 0; i < b->probs.size(); ++i) {
+        const bool done = ck.raster_total[i] > 0 && ck.raster_done[i] == ck.raster_total[i] &&
+                          ck.guid_done[i] == ck.guid_total[i] && ck.t_reduce[i] != 0;
+        const unsigned long long tr = ck.t_raster[i] > ck.t_guid[i] ? ck.t_raster[i] : ck.t_guid[i];
+        if (records_ms) records_ms[i] = done ? (double)(long long)(tr - ck.t0) * 1e-6 : -1.0;
+        if (objectives_ms) objectives_ms[i] = done ? (double)(long long)(ck.t_reduce[i] - ck.t0) * 1e-6 : -1.0;
+    }
+    return MOREA_OK;
 }
 
 morea_status morea_batch_set_launch(morea_batch *b, int32_t blocks_per_sm, int32_t chunk)

@@ -193,4 +193,12 @@ __device__ __forceinline__ void make_setup(const int4 *own, const int4 *oth, con
     su.t0[2] = oth[0].z * inv_s - 0.5f;
 }
 
+// A large item of the image pass: an unfolded copy whose bounding box holds
+// at least kBigItemVoxels voxel centres.
+__device__ __forceinline__ bool item_is_big(const RasterSetup &su)
+{
+    return (su.valid & 1) && (long long)max(su.ihi - su.ilo + 1, 0) * max(su.jhi - su.jlo + 1, 0) *
+                                     max(su.khi - su.klo + 1, 0) >= kBigItemVoxels;
+}
+
 }  // namespace morea

@@ -15,6 +15,28 @@ namespace morea {
 constexpr int kMaxGroups = 8;
 constexpr int kBlock = 256;
 
+constexpr int kMaxBatch = 64;
+
+// Completion clock of a batched evaluation (morea_batch_*), per problem of
+// the batch: its items counted as the passes finish them, and the
+// %globaltimer (ns) at which its last image-pass item, its last guidance item
+// and its last objective reduction finished; t0 is stamped by the first
+// kernel of the batch.
+struct BatchClock {
+    unsigned long long t0;
+    unsigned long long t_raster[kMaxBatch], t_guid[kMaxBatch], t_reduce[kMaxBatch];
+    int raster_done[kMaxBatch], raster_total[kMaxBatch];
+    int guid_done[kMaxBatch], guid_total[kMaxBatch];
+    int reduce_done[kMaxBatch];
+};
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // Everything a kernel needs to know about one registration problem.  Lives in
 // device memory (one per problem) so batched launches can mix problems.
 struct DevProblem {
@@ -46,6 +68,7 @@ struct DevProblem {
     morea_tet_record *cache;         // [max_sol][T]
     morea_totals *totals;            // [max_sol]
     unsigned int *status;            // device status word
+    BatchClock *clock;               // batched evaluation only (the batch's copy): completion clock, else NULL
 };
 
 // One (solution or request, tet) work unit with both copies' snapped vertices.
@@ -115,8 +138,6 @@ struct BatchProb {
     int n_sol;
 };
 
-constexpr int kMaxBatch = 64;
-
 // Passed by value to the batch kernels (kernel parameters are copied at
 // launch, so no host buffer has to outlive the call or a captured graph).
 struct BatchTable {
@@ -147,15 +168,15 @@ cudaError_t launch_band_rows(const DevProblem &hp, int side, short2 *bandrow, cu
 // image pass (+ continuous guidance pass); bandrows: [2 * entries][kBandRowsPerItem] scratch
 constexpr int kBandRowsPerItem = 128;
 // chunk > 0 selects the atomic work queue.  queue: kQueueList device counters
-// (reset here), then the list of the (entry, side) items that have band rows
-// (continuous guidance; capacity 2 * n_entries_host), then the order in
-// which the image pass takes its items (2 * n_entries_host: the copies with
-// the largest bounding boxes first).
+// (the first kQueueOrderBig reset by launch_raster, the large-item count by
+// the caller before the entry pass), then the list of the (entry, side)
+// items that have band rows
+// (continuous guidance; capacity 2 * n_entries_host), then the list of the
+// large items the image pass takes first (capacity 2 * n_entries_host).
 constexpr int kQueueRaster = 0;      // work counter of the image pass
 constexpr int kQueueGuidance = 1;    // work counter of the guidance pass
 constexpr int kQueueListCount = 2;   // items listed for the guidance pass
-constexpr int kQueueOrderBig = 3;    // large items placed in the order, from the front
-constexpr int kQueueOrderSmall = 4;  // the others, from the back
+constexpr int kQueueOrderBig = 3;    // large items listed for the image pass to take first
 constexpr int kQueueList = 8;        // first list entry (32-byte aligned)
 // A copy whose bounding box holds at least this many voxel centres is an
 // item the ordered image pass takes first.
@@ -201,7 +222,8 @@ cudaError_t launch_repair(const DevProblem *dp, const DevProblem &hp, const int 
                           int *moved, double *severity, cudaStream_t st);
 cudaError_t launch_raster(const DevProblem *probs, const DevProblem &hp, const WorkEntry *entries,
                           const RasterSetup *setup, RasterOut *rout, int2 *bandrows, const int *n_entries_dev,
-                          int n_entries_host, int grid, int chunk, int *queue, bool ordered, cudaStream_t st);
+                          int n_entries_host, int grid, int chunk, int *queue, bool ordered, BatchClock *clock,
+                          cudaStream_t st);
 cudaError_t launch_reduce_full(const DevProblem *dp, const DevProblem &hp, int n_sol, const int *slot,
                                const TetOut *tout, const RasterOut *rout, double *obj, uint8_t *folded,
                                double *severity, cudaStream_t st);

@@ -41,7 +41,7 @@ ENTRY_POINTS = (
     "morea_parallel_groups", "morea_init_noise", "morea_warp_labels", "morea_cluster", "morea_slot_objectives",
     "morea_sample_elements_workspace", "morea_sample_elements", "morea_surface_distance_workspace", "morea_surface_distance",
     "morea_device_status", "morea_problem_info", "morea_batch_create", "morea_batch_destroy",
-    "morea_batch_eval_full", "morea_batch_capture", "morea_batch_replay", "morea_set_launch",
+    "morea_batch_eval_full", "morea_batch_capture", "morea_batch_replay", "morea_batch_latency", "morea_set_launch",
     "morea_batch_set_launch", "morea_profile", "morea_profile_read", "morea_fold_magnitude_noalloc",
     "morea_status_string",
 )
@@ -132,6 +132,7 @@ def lib():
     L.morea_batch_eval_full.argtypes = [vp, ctypes.POINTER(i32), pa, pa, pa, pa, pa, vp]
     L.morea_batch_capture.argtypes = [vp, ctypes.POINTER(i32), pa, pa, pa, pa, pa, vp]
     L.morea_batch_replay.argtypes = [vp, vp]
+    L.morea_batch_latency.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     L.morea_set_launch.argtypes = [vp, i32, i32]
     L.morea_batch_set_launch.argtypes = [vp, i32, i32]
     L.morea_profile.argtypes = [vp, ctypes.c_uint32]
@@ -622,6 +623,15 @@ class Batch:
 
     def replay(self, stream=None):
         _check(lib().morea_batch_replay(self._h, _stream(stream)), "morea_batch_replay")
+
+    def latency(self):
+        """Per-problem completion of the last evaluation, ms after it started:
+        (records complete, objectives written), as numpy arrays (-1: not
+        complete).  Synchronises the device."""
+        n = len(self.problems)
+        rec, obj = (ctypes.c_double * n)(), (ctypes.c_double * n)()
+        _check(lib().morea_batch_latency(self._h, rec, obj), "morea_batch_latency")
+        return np.array(rec[:]), np.array(obj[:])
 
     def set_launch(self, blocks_per_sm: int, chunk: int):
         _check(lib().morea_batch_set_launch(self._h, int(blocks_per_sm), int(chunk)), "morea_batch_set_launch")

@@ -148,3 +148,36 @@ def test_batch_rejects_mixed_modes(mo):
         mo.Batch([a, b])
     with pytest.raises(mo.MoreaError):
         mo.Batch([a, a])
+
+
+def test_batch_latency_per_problem(mo):
+    """The batch's completion clock: every problem's records are complete
+    before its objectives are written, both within the evaluation's own time
+    (CUDA events around it), and problems of different sizes complete at
+    different times; a graph replay stamps them again."""
+    probs = _problems()
+    gps = [mo.Problem(p) for p in probs]
+    batch = mo.Batch(gps)
+    srcs = [torch.as_tensor(p.sol_src).cuda() for p in probs]
+    tgts = [torch.as_tensor(p.sol_tgt).cuda() for p in probs]
+    outs = mo.Batch.outputs(srcs)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        batch.eval_full(srcs, tgts, outs, stream=stream)
+        batch.capture(srcs, tgts, outs, stream)
+    stream.synchronize()
+    for run in range(2):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            a.record(stream)
+            if run == 0:
+                batch.eval_full(srcs, tgts, outs, stream=stream)
+            else:
+                batch.replay(stream)
+            b.record(stream)
+        b.synchronize()
+        total = a.elapsed_time(b)
+        rec, obj = batch.latency()
+        assert (rec > 0).all() and (obj >= rec).all(), (rec, obj)
+        assert obj.max() <= total * 1.05 + 0.05, (obj, total)
+        assert len(np.unique(np.round(rec, 4))) > 1
