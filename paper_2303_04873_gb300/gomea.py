@@ -29,6 +29,15 @@ A generation:
 
 The initial population comes from ``Problem.init_noise`` (Sec. 4.2.2).
 Without repair, folded candidates are discarded (Sec. 4.3.1).
+
+Optional learned pre-screen (not in the paper): with a ``surrogate``
+(``ea.Surrogate``) only the ``screen`` fraction of each group's requests
+with the best predicted change -- net(candidate) - net(parent), summed over
+objectives in units of the training targets' standard deviation, lowest
+first (reading R11) -- is evaluated exactly; the others count as rejected.
+``random_screen`` evaluates a random fraction of the same size instead.
+``log`` collects (features, objectives) of up to ``log_per_group`` exactly
+evaluated requests per group, for training a surrogate.
 """
 
 from __future__ import annotations
@@ -84,8 +93,13 @@ class Gomea:
     requests and max_changed(cfg) changed points per request."""
 
     def __init__(self, gp: "morea.Problem", prob, n_pop: int, cfg: Optional[GomeaConfig] = None, seed: int = 0,
-                 start_src: Optional[np.ndarray] = None, start_tgt: Optional[np.ndarray] = None):
+                 start_src: Optional[np.ndarray] = None, start_tgt: Optional[np.ndarray] = None,
+                 surrogate=None, screen: float = 0.25, random_screen: bool = False, log: Optional[list] = None,
+                 log_per_group: int = 128):
         self.gp, self.cfg = gp, cfg or GomeaConfig()
+        self.surrogate, self.screen, self.random_screen = surrogate, float(screen), bool(random_screen)
+        self.log, self.log_per_group = log, int(log_per_group)
+        self.exact = 0                   # exact evaluations (requests, repaired candidates, the initial population)
         self.rng = np.random.default_rng(seed)
         self.dev_rng = torch.Generator(device="cuda")     # the repair's trial draws
         self.dev_rng.manual_seed(int(seed))
@@ -115,6 +129,7 @@ class Gomea:
             T = torch.as_tensor(np.ascontiguousarray(start_tgt, np.float32)).to(self.dev)
         self.S, self.T = S, T
         obj, folded, _ = gp.eval_full(S, T)
+        self.exact += self.n
         self.obj = obj.cpu().numpy()
         self.folded = folded.cpu().numpy().astype(bool)
         self.archive = Archive(self.cfg.archive_cap)
@@ -210,6 +225,40 @@ class Gomea:
             self.T[sol_d[own[sel]], pi[sel]] = ct[sel]
         return sols[keep][acc.astype(bool)], len(keep), int(acc.sum())
 
+    def _features(self, sol: torch.Tensor, pts: torch.Tensor, cs: torch.Tensor, ct: torch.Tensor,
+                  chunk: int = 4096) -> list:
+        """Displacement features of two-point requests (solution sol[r], points
+        pts[2r:2r+2] moved to cs / ct), in chunks of `chunk` requests."""
+        out = []
+        n = int(sol.shape[0])
+        for a in range(0, n, chunk):
+            b = min(n, a + chunk)
+            off = torch.arange(0, 2 * (b - a) + 1, 2, dtype=torch.int32, device=self.dev)
+            out.append(self.gp.partial_features(sol[a:b].int().contiguous(), off, pts[2 * a:2 * b].contiguous(),
+                                                cs[2 * a:2 * b].contiguous(), ct[2 * a:2 * b].contiguous()))
+        return out
+
+    def _screen(self, d, gel, new_s, new_t, n_req: int) -> np.ndarray:
+        """Indices of the requests to evaluate exactly (all without a screen)."""
+        if self.surrogate is None and not self.random_screen:
+            return np.arange(n_req)
+        k = max(1, int(round(self.screen * n_req)))
+        if self.surrogate is None:
+            return np.sort(self.rng.choice(n_req, size=k, replace=False))
+        sur = self.surrogate
+        # each solution's own field through the network (its committed slot; the
+        # "change" of one point to its current value leaves it as it is)
+        sol_all = torch.arange(self.n, dtype=torch.int32, device=self.dev)
+        off1 = torch.arange(0, self.n + 1, dtype=torch.int32, device=self.dev)
+        p0 = torch.zeros(self.n, dtype=torch.int32, device=self.dev)
+        parent = sur.predict(self.gp.partial_features(sol_all, off1, p0, self.S[:, 0].contiguous(),
+                                                      self.T[:, 0].contiguous()))
+        pts = gel[d[2].long()].reshape(-1)
+        cand = np.concatenate([sur.predict(f) for f in self._features(d[0], pts, new_s, new_t)])
+        req_sol = d[0].cpu().numpy()
+        score = ((cand - parent[req_sol]) / sur.std).sum(axis=1)
+        return np.sort(np.argsort(score, kind="stable")[:k])
+
     def step(self) -> dict:
         """One generation; returns its counts."""
         c = self.cfg
@@ -229,11 +278,28 @@ class Gomea:
             d = [torch.as_tensor(a).to(self.dev) for a in (req_sol, req_cl, req_el, z)]
             new_s, new_t = self.gp.sample_elements(self.S, self.T, mem_d, gel, cm_d, d[0], d[1], d[2], d[3],
                                                    fixed=self.fixed, work=self.work)
+            chosen = self._screen(d, gel, new_s, new_t, n_req)
+            if len(chosen) < n_req:          # only the screened requests are evaluated exactly
+                ch = torch.as_tensor(chosen).to(self.dev)
+                rows2 = torch.stack([2 * ch, 2 * ch + 1], 1).reshape(-1)
+                d = [x[ch] for x in d]
+                new_s, new_t = new_s[rows2].contiguous(), new_t[rows2].contiguous()
+                req_sol, req_el, req_cl = req_sol[chosen], req_el[chosen], req_cl[chosen]
+                n_req = len(chosen)
             off = torch.arange(0, 2 * n_req + 1, 2, dtype=torch.int32, device=self.dev)
             pts = gel[d[2].long()].reshape(-1).contiguous()
             o, f, _ = self.gp.eval_partial(d[0], off, pts, new_s, new_t)
+            self.exact += n_req
             o = o.cpu().numpy()
             f = f.cpu().numpy().astype(bool)
+            if self.log is not None:         # a sample of this group's exact evaluations, before the commit
+                okr = np.nonzero(np.all(np.isfinite(o), axis=1))[0]
+                take = np.sort(self.rng.choice(okr, size=min(self.log_per_group, len(okr)), replace=False))
+                if len(take):
+                    tk = torch.as_tensor(take).to(self.dev)
+                    rows2 = torch.stack([2 * tk, 2 * tk + 1], 1).reshape(-1)
+                    fe = self._features(d[0][tk], pts[rows2], new_s[rows2], new_t[rows2])
+                    self.log.append((torch.cat(fe), o[take].copy()))
             hi = self.window_hi() if steer else np.inf
             acc = self._accept(o, f, req_sol, hi).astype(np.uint8)
             self.gp.commit_partial(torch.as_tensor(acc).to(self.dev))
@@ -260,6 +326,7 @@ class Gomea:
                     hit[np.unique(pop_cluster[rsol])] = True
                 self.repaired += n_rep
                 self.repaired_accepted += n_racc
+                self.exact += n_rep
                 n_acc += n_racc
             n_req_total += n_req
             n_acc_total += n_acc

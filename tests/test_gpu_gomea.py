@@ -207,3 +207,39 @@ def test_generations_on_the_full_size_problem(mo):
         np.testing.assert_array_equal(X[:, fx], np.broadcast_to(p.ref_points[fx], (n,) + p.ref_points[fx].shape))
     _pareto_ok(run.archive.pts)
     assert gp.device_status() == 0
+
+
+def test_screened_generations(mo):
+    """The learned and the random pre-screen evaluate exactly round(0.25 n m)
+    requests per group of m elements (plus the population and the repaired
+    candidates), and the committed objectives still equal a fresh
+    evaluation of the device coordinates."""
+    from paper_2303_04873_gb300 import ea, gomea
+    p = synth.make_c0(n_sol=1)
+    n = 16
+    cfg = gomea.GomeaConfig(clusters=4, steer_at=1000, init_kernels=4, init_rounds=20, init_sigma=(3.0, 9.0),
+                            init_strength=(0.05, 0.2), repair=False)
+    gp = mo.Problem(p, max_solutions=n, max_requests=gomea.max_requests(p, n), max_changed=gomea.max_changed(cfg))
+    log = []
+    data = gomea.Gomea(gp, p, n, cfg, seed=7, log=log, log_per_group=64)
+    for _ in range(3):
+        data.step()
+    feats = torch.cat([f for f, _ in log])
+    targ = np.concatenate([o for _, o in log])
+    assert feats.shape == (len(targ), 3 * p.n_points)
+    net = mo.Mlp(3 * p.n_points, 64, 64, 3, max_batch=256, seed=0)
+    tr = ea.train_surrogate(net, feats, targ, epochs=2, lr=1e-3)
+    per_gen = sum(max(1, int(round(0.25 * n * len(g)))) for g in data.groups)
+    for kind in ("surrogate", "random"):
+        run = gomea.Gomea(gp, p, n, cfg, seed=8, surrogate=tr["surrogate"] if kind == "surrogate" else None,
+                          random_screen=kind == "random")
+        for _ in range(2):
+            st = run.step()
+            assert st["requests"] == per_gen
+        assert run.exact == n + 2 * per_gen
+        fresh = mo.Problem(p, max_solutions=n)
+        o, f, _ = fresh.eval_full(run.S, run.T)
+        np.testing.assert_allclose(o.cpu().numpy(), run.obj, rtol=1e-9)
+        assert not f.cpu().numpy().any()
+        _pareto_ok(run.archive.pts)
+    assert gp.device_status() == 0
