@@ -26,26 +26,6 @@ namespace morea {
 
 namespace {
 
-// Continuous guidance term of one voxel that lies in at least one band.
-__device__ __forceinline__ void guidance_voxel(const DevProblem &P, int side, int idx, float yx, float yy, float yz,
-                                            float &s_g, float &c_g)
-{
-    const int nx = P.nx, ny = P.ny, nz = P.nz;
-    unsigned mk = P.band[side][idx];
-    while (mk) {
-        const int g = __ffs(mk) - 1;
-        mk &= mk - 1;
-        const size_t off = (size_t)g * ((size_t)nx * ny * nz);
-        const float av = __ldg(P.dmap[side] + off + idx);
-        if (av < P.r) {
-            const float dv = trilin_plain(P.dmap[1 - side] + off, nx, ny, nz, yx, yy, yz);
-            const float w = P.wgt[g] * (P.r - av) * P.inv_r;
-            const float df = av - dv;
-            kadd(s_g, c_g, w * df * df);
-        }
-    }
-}
-
 // Pair-transfer guidance of one tet copy: the guidance points of this side
 // located in the copy (exact perturbed inside test on their snapped
 // coordinates), mapped and compared with their partners.
@@ -338,6 +318,61 @@ __global__ void __launch_bounds__(kBlock, 6) k_raster(const DevProblem *__restri
     });
 }
 
+// Continuous guidance term of one band voxel, in two parts so that a lane
+// can load the samples of several voxels before it sums any of them.
+// band_load maps the voxel x of row (j, k) = (ojk & 0xffff, ojk >> 16),
+// whose band record is r, by the copy's affine map (M = m0.xyz / m0.w m1.xy
+// / m1.zw m2.x, s0 = m2.yzw, t0 = t4.xyz) and samples the other side's
+// distance map of the lowest band group; band_sum adds that group's term and
+// then the terms of the voxel's other groups, lowest first.
+struct BandVoxel {
+    int idx;                              // voxel index in the own image
+    unsigned mk;                          // band groups still to add (lowest first)
+    float av, dv;                         // own distance and sampled distance of the lowest group
+    float yx, yy, yz;                     // mapped position
+};
+
+__device__ __forceinline__ BandVoxel band_load(const DevProblem &P, int side, float4 m0, float4 m1, float4 m2,
+                                               float4 t4, int2 r, int ojk)
+{
+    BandVoxel b;
+    const int x = r.x & 0xffff;
+    const int oj = ojk & 0xffff, okk = ojk >> 16;
+    const int nx = P.nx, ny = P.ny, nz = P.nz;
+    b.idx = (okk * ny + oj) * nx + x;
+    const float dx = (float)x - m2.y, dy = (float)oj - m2.z, dz = (float)okk - m2.w;
+    b.yx = fmaf(m0.x, dx, fmaf(m0.y, dy, fmaf(m0.z, dz, t4.x)));
+    b.yy = fmaf(m0.w, dx, fmaf(m1.x, dy, fmaf(m1.y, dz, t4.y)));
+    b.yz = fmaf(m1.z, dx, fmaf(m1.w, dy, fmaf(m2.x, dz, t4.z)));
+    b.mk = (unsigned)r.x >> 16;
+    b.av = __int_as_float(r.y);
+    const int g = __ffs(b.mk) - 1;
+    b.dv = trilin_plain(P.dmap[1 - side] + (size_t)g * ((size_t)nx * ny * nz), nx, ny, nz, b.yx, b.yy, b.yz);
+    return b;
+}
+
+__device__ __forceinline__ void band_sum(const DevProblem &P, int side, BandVoxel b, float &s_g, float &c_g)
+{
+    const int nx = P.nx, ny = P.ny, nz = P.nz;
+    const size_t n_vox = (size_t)nx * ny * nz;
+    unsigned mk = b.mk;
+    float av = b.av, dv = b.dv;
+    while (mk) {
+        const int g = __ffs(mk) - 1;
+        mk &= mk - 1;
+        if (av < P.r) {
+            const float w = P.wgt[g] * (P.r - av) * P.inv_r;
+            const float df = av - dv;
+            kadd(s_g, c_g, w * df * df);
+        }
+        if (mk) {
+            const size_t off = (size_t)(__ffs(mk) - 1) * n_vox;
+            av = __ldg(P.dmap[side] + off + b.idx);
+            dv = trilin_plain(P.dmap[1 - side] + off, nx, ny, nz, b.yx, b.yy, b.yz);
+        }
+    }
+}
+
 // Continuous guidance (a6): for every (entry, side) that the image pass listed
 // as having band rows, the band voxels of those rows (rows recorded by the image pass, or recomputed when
 // there were more than kBandRows; band voxels from the per-row sorted
@@ -428,26 +463,31 @@ __global__ void __launch_bounds__(kBlock, 4) k_guidance(const DevProblem *__rest
             const int total = __shfl_sync(FULL, incl, 31);
             const int d = a - (incl - cnt);           // list position = d + v
             const int jk = j | (k << 16);
-            for (int vb = 0; vb < total; vb += 32) {
-                const int v = vb + lane;
+            // two 32-voxel chunks per pass: both chunks' records and samples are
+            // loaded before either is summed; the lane sums voxel vb + lane, then
+            // vb + 32 + lane, the order of one chunk per pass
+            auto owner = [&](int v) {
                 int ow = 0;
 #pragma unroll
                 for (int step = 16; step >= 1; step >>= 1) {
                     const int p = __shfl_sync(FULL, incl, ow + step - 1);
                     if (p <= v) ow += step;
                 }
-                const int od = __shfl_sync(FULL, d, ow);
-                const int ojk = __shfl_sync(FULL, jk, ow);
-                if (v < total) {
-                    const int x = P.band_x[side][od + v];
-                    const int oj = ojk & 0xffff, okk = ojk >> 16;
-                    const int idx = (okk * ny + oj) * nx + x;
-                    const float dx = (float)x - m2.y, dy = (float)oj - m2.z, dz = (float)okk - m2.w;
-                    const float yx = fmaf(m0.x, dx, fmaf(m0.y, dy, fmaf(m0.z, dz, t4.x)));
-                    const float yy = fmaf(m0.w, dx, fmaf(m1.x, dy, fmaf(m1.y, dz, t4.y)));
-                    const float yz = fmaf(m1.z, dx, fmaf(m1.w, dy, fmaf(m2.x, dz, t4.z)));
-                    guidance_voxel(P, side, idx, yx, yy, yz, s_g, c_g);
-                }
+                return ow;
+            };
+            for (int vb = 0; vb < total; vb += 64) {
+                const int v0 = vb + lane, v1 = vb + 32 + lane;
+                const int ow0 = owner(v0), ow1 = owner(v1);
+                const int od0 = __shfl_sync(FULL, d, ow0), ojk0 = __shfl_sync(FULL, jk, ow0);
+                const int od1 = __shfl_sync(FULL, d, ow1), ojk1 = __shfl_sync(FULL, jk, ow1);
+                int2 r0 = make_int2(0, 0), r1 = make_int2(0, 0);
+                if (v0 < total) r0 = __ldg(P.band_rec[side] + od0 + v0);
+                if (v1 < total) r1 = __ldg(P.band_rec[side] + od1 + v1);
+                BandVoxel b0, b1;
+                if (v0 < total) b0 = band_load(P, side, m0, m1, m2, t4, r0, ojk0);
+                if (v1 < total) b1 = band_load(P, side, m0, m1, m2, t4, r1, ojk1);
+                if (v0 < total) band_sum(P, side, b0, s_g, c_g);
+                if (v1 < total) band_sum(P, side, b1, s_g, c_g);
             }
         }
         const float e_g = warp_comp_sum(s_g, -c_g);

@@ -642,6 +642,21 @@ __global__ void __launch_bounds__(kBlock) k_band_rows(const uint8_t *__restrict_
     }
 }
 
+// Distance word of each band record: the voxel's own distance to the lowest
+// guidance group whose band holds it (the first term of its guidance sum).
+__global__ void __launch_bounds__(kBlock) k_band_records(const float *__restrict__ dmap, const int *__restrict__ start,
+                                                        int nx, int rows, size_t n_vox, int2 *rec)
+{
+    for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < rows; row += gridDim.x * blockDim.x) {
+        const int a = start[row], b = start[row + 1];
+        for (int i = a; i < b; ++i) {
+            const int2 r = rec[i];
+            const int x = r.x & 0xffff, g = __ffs(r.x >> 16) - 1;
+            rec[i].y = __float_as_int(dmap[(size_t)g * n_vox + (size_t)row * nx + x]);
+        }
+    }
+}
+
 // Surrogate input of each partial candidate: per vertex the displacement
 // target - source (voxel units, snapped coordinates) of the slot's committed
 // solution with the request's moved points replaced.
@@ -747,6 +762,14 @@ cudaError_t launch_build_quads(const DevProblem &hp, int side, void *quad, cudaS
 cudaError_t launch_band_rows(const DevProblem &hp, int side, short2 *bandrow, cudaStream_t st)
 {
     k_band_rows<<<grid_for((long long)hp.ny * hp.nz), kBlock, 0, st>>>(hp.band[side], hp.nx, hp.ny, hp.nz, bandrow);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_band_records(const DevProblem &hp, int side, int2 *rec, cudaStream_t st)
+{
+    const int rows = hp.ny * hp.nz;
+    k_band_records<<<grid_for(rows), kBlock, 0, st>>>(hp.dmap[side], hp.band_start[side], hp.nx, rows,
+                                                      (size_t)hp.nx * hp.ny * hp.nz, rec);
     return cudaGetLastError();
 }
 

@@ -443,32 +443,35 @@ morea_status morea_create_problem(const morea_problem_desc *d, void *stream, mor
             TRY(cudaMemcpyAsync(hband.data(), band[s], (size_t)N, cudaMemcpyDeviceToHost, st));
             TRY(cudaStreamSynchronize(st));
             std::vector<int> start((size_t)ny * nz + 1, 0);
-            std::vector<short> xs, rank((size_t)N);
+            std::vector<int2> recs;
+            std::vector<short> rank((size_t)N);
             for (long long row = 0; row < (long long)ny * nz; ++row) {
                 const uint8_t *b = hband.data() + row * nx;
                 short before = 0;
                 for (int x = 0; x < nx; ++x) {
                     rank[(size_t)row * nx + x] = before;
                     if (b[x]) {
-                        xs.push_back((short)x);
+                        recs.push_back(make_int2(x | ((int)b[x] << 16), 0));
                         ++before;
                     }
                 }
-                start[row + 1] = (int)xs.size();
+                start[row + 1] = (int)recs.size();
             }
             int *bs = nullptr;
-            short *bxs = nullptr, *brk = nullptr;
+            int2 *brc = nullptr;
+            short *brk = nullptr;
             TRY(dalloc(p, &bs, start.size()));
-            TRY(dalloc(p, &bxs, std::max<size_t>(xs.size(), 1)));
+            TRY(dalloc(p, &brc, std::max<size_t>(recs.size(), 1)));
             TRY(dalloc(p, &brk, (size_t)N));
             TRY(cudaMemcpyAsync(bs, start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice, st));
-            if (!xs.empty())
-                TRY(cudaMemcpyAsync(bxs, xs.data(), sizeof(short) * xs.size(), cudaMemcpyHostToDevice, st));
+            if (!recs.empty())
+                TRY(cudaMemcpyAsync(brc, recs.data(), sizeof(int2) * recs.size(), cudaMemcpyHostToDevice, st));
             TRY(cudaMemcpyAsync(brk, rank.data(), sizeof(short) * (size_t)N, cudaMemcpyHostToDevice, st));
-            TRY(cudaStreamSynchronize(st));
             hp.band_start[s] = bs;
-            hp.band_x[s] = bxs;
+            hp.band_rec[s] = brc;
             hp.band_rank[s] = brk;
+            TRY(launch_band_records(hp, s, brc, st));
+            TRY(cudaStreamSynchronize(st));
         }
         TRY(cudaMemcpyAsync(p->dp, &hp, sizeof(DevProblem), cudaMemcpyHostToDevice, st));
     }

@@ -54,7 +54,8 @@ struct DevProblem {
     const uint8_t *band[2];          // [N] bit g set where dmap[side][g] < r
     const short2 *bandrow[2];        // [nz*ny] x-range of band voxels in each image row (empty: x > y)
     const int *band_start[2];        // [nz*ny + 1] CSR of the band voxels of each image row
-    const short *band_x[2];          // their x, ascending within a row
+    const int2 *band_rec[2];         // per band voxel: x | band bits << 16, and the bits of its own distance
+                                     // to the lowest band group; ascending x within a row
     const short *band_rank[2];       // [N] band voxels before x in the same image row
     const uint8_t *bandd[2];         // [N] band bits OR-ed over the 2x2x2 cell at each voxel (sampled)
     const int4 *tets;                // positively oriented topology
@@ -165,6 +166,8 @@ cudaError_t launch_entry_work(const DevProblem *dp, const WorkEntry *entries, Ra
                               const int *n_entries_dev, int n_entries_host, int *rqueue, cudaStream_t st);
 cudaError_t launch_build_quads(const DevProblem &hp, int side, void *quad, cudaStream_t st);
 cudaError_t launch_band_rows(const DevProblem &hp, int side, short2 *bandrow, cudaStream_t st);
+// fills the distance word of the band records of one side (x and bits set by the host)
+cudaError_t launch_band_records(const DevProblem &hp, int side, int2 *rec, cudaStream_t st);
 // image pass (+ continuous guidance pass); bandrows: [2 * entries][kBandRowsPerItem] scratch
 constexpr int kBandRowsPerItem = 128;
 // chunk > 0 selects the atomic work queue.  queue: kQueueList device counters
@@ -180,7 +183,7 @@ constexpr int kQueueOrderBig = 3;    // large items listed for the image pass to
 constexpr int kQueueList = 8;        // first list entry (32-byte aligned)
 // A copy whose bounding box holds at least this many voxel centres is an
 // item the ordered image pass takes first.
-constexpr int kBigItemVoxels = 16384;
+constexpr int kBigItemVoxels = 32768;
 inline size_t queue_ints(long long cap_entries, bool continuous)
 {
     (void)continuous;
