@@ -49,7 +49,9 @@ __device__ __forceinline__ void ld_quad(const uint2 *q, int idx, float &a, float
 }
 
 // Trilinear sample with the position clamped to [0, n-1] per axis and the
-// cell i0 = min(floor(y), n - 2), from the quad copy of the image.
+// cell i0 = min(floor(y), n - 2), from the quad copy of the image (q at the
+// element of cell (0, 0, 0); row stride nx + 1, plane stride
+// (nx + 1)(ny + 1)).
 template <typename QT>
 __device__ __forceinline__ float trilin_quad(const QT *q, int nx, int ny, int nz, float yx, float yy, float yz)
 {
@@ -58,27 +60,32 @@ __device__ __forceinline__ float trilin_quad(const QT *q, int nx, int ny, int nz
     const float cz = fminf(fmaxf(yz, 0.0f), (float)(nz - 1));
     const int ix = min((int)cx, nx - 2), iy = min((int)cy, ny - 2), iz = min((int)cz, nz - 2);
     const float fx = cx - (float)ix, fy = cy - (float)iy, fz = cz - (float)iz;
-    const int b = (iz * ny + iy) * nx + ix;
+    const int sx = nx + 1, sxy = (nx + 1) * (ny + 1);
+    const int b = iz * sxy + iy * sx + ix;
     float v000, v100, v010, v110, v001, v101, v011, v111;
     ld_quad(q, b, v000, v100, v010, v110);
-    ld_quad(q, b + nx * ny, v001, v101, v011, v111);
+    ld_quad(q, b + sxy, v001, v101, v011, v111);
     const float c00 = fmaf(fx, v100 - v000, v000), c10 = fmaf(fx, v110 - v010, v010);
     const float c01 = fmaf(fx, v101 - v001, v001), c11 = fmaf(fx, v111 - v011, v011);
     const float c0 = fmaf(fy, c10 - c00, c00), c1 = fmaf(fy, c11 - c01, c01);
     return fmaf(fz, c1 - c0, c0);
 }
 
-// The same sample when the position is known to lie strictly inside
-// [0, n-1] per axis: the clamps and the last-cell guard are no-ops there.
+// The same sample when the position is known to lie in [-1, n) per axis:
+// the padding of the quad copy repeats the edge values, so the cell
+// floor(y) (from -1 to n - 1) gives the clamped sample without clamping:
+// outside [0, n - 1] both corners of an axis hold the edge value, inside it
+// the cell and weights are those of the clamped form.  sx = nx + 1,
+// sxy = (nx + 1)(ny + 1).
 template <typename QT>
-__device__ __forceinline__ float trilin_quad_inner(const QT *q, int nx, int ny, float yx, float yy, float yz)
+__device__ __forceinline__ float trilin_quad_inner(const QT *q, int sx, int sxy, float yx, float yy, float yz)
 {
-    const int ix = (int)yx, iy = (int)yy, iz = (int)yz;
+    const int ix = __float2int_rd(yx), iy = __float2int_rd(yy), iz = __float2int_rd(yz);
     const float fx = yx - (float)ix, fy = yy - (float)iy, fz = yz - (float)iz;
-    const int b = (iz * ny + iy) * nx + ix;
+    const int b = iz * sxy + iy * sx + ix;
     float v000, v100, v010, v110, v001, v101, v011, v111;
     ld_quad(q, b, v000, v100, v010, v110);
-    ld_quad(q, b + nx * ny, v001, v101, v011, v111);
+    ld_quad(q, b + sxy, v001, v101, v011, v111);
     const float c00 = fmaf(fx, v100 - v000, v000), c10 = fmaf(fx, v110 - v010, v010);
     const float c01 = fmaf(fx, v101 - v001, v001), c11 = fmaf(fx, v111 - v011, v011);
     const float c0 = fmaf(fy, c10 - c00, c00), c1 = fmaf(fy, c11 - c01, c01);

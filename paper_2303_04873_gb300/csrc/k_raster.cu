@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(kBlock, 6) k_raster(const DevProblem *__restri
                 const float yx = fmaf(M00, dx, rx);
                 const float yy = fmaf(M10, dx, ry);
                 const float yz = fmaf(M20, dx, rz);
-                const float b = inner ? trilin_quad_inner(oq, nx, ny, yx, yy, yz)
+                const float b = inner ? trilin_quad_inner(oq, nx + 1, (nx + 1) * (ny + 1), yx, yy, yz)
                                       : trilin_quad(oq, nx, ny, nz, yx, yy, yz);
                 kadd(s_img, c_img, hfun<HMODE>(a, b));
             };

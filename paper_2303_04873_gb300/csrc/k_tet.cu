@@ -591,37 +591,39 @@ __global__ void __launch_bounds__(kBlock) k_count_visits(const RasterOut *__rest
     if (threadIdx.x == 0 && c) atomicAdd(visits, c);
 }
 
-// The gather copy of an image: per voxel the four values (x, y), (x+1, y),
-// (x, y+1), (x+1, y+1) of its z-plane (indices clamped at the last row and
-// column, which the trilinear cell never uses), so one 16-byte (FP32) or
-// 8-byte (FP16) load brings one plane of the 2x2x2 neighbourhood.
+// Quad copy (quad_cells layout): one element per padded cell, the four
+// values of its z-plane with every index clamped into the image, so one
+// 16-byte (FP32) or 8-byte (FP16) load brings one plane of the 2x2x2
+// neighbourhood of any position in [-1, n) per axis.
 template <typename TI, typename QT>
-__global__ void __launch_bounds__(kBlock) k_build_quads(const TI *__restrict__ img, int nx, int ny, int nz, QT *quad);
+__device__ __forceinline__ QT quad_of(const TI *img, int i00, int i10, int i01, int i11);
 
 template <>
-__global__ void __launch_bounds__(kBlock) k_build_quads<float, float4>(const float *__restrict__ img, int nx, int ny,
-                                                                      int nz, float4 *quad)
+__device__ __forceinline__ float4 quad_of<float, float4>(const float *img, int i00, int i10, int i01, int i11)
 {
-    const long long N = (long long)nx * ny * nz;
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < N;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(idx % nx), y = (int)((idx / nx) % ny);
-        const long long dx = x + 1 < nx ? 1 : 0, dy = y + 1 < ny ? nx : 0;
-        quad[idx] = make_float4(img[idx], img[idx + dx], img[idx + dy], img[idx + dx + dy]);
-    }
+    return make_float4(img[i00], img[i10], img[i01], img[i11]);
 }
 
 template <>
-__global__ void __launch_bounds__(kBlock) k_build_quads<unsigned short, uint2>(const unsigned short *__restrict__ img,
-                                                                              int nx, int ny, int nz, uint2 *quad)
+__device__ __forceinline__ uint2 quad_of<unsigned short, uint2>(const unsigned short *img, int i00, int i10, int i01,
+                                                              int i11)
 {
-    const long long N = (long long)nx * ny * nz;
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < N;
+    return make_uint2((unsigned)img[i00] | ((unsigned)img[i10] << 16), (unsigned)img[i01] | ((unsigned)img[i11] << 16));
+}
+
+template <typename TI, typename QT>
+__global__ void __launch_bounds__(kBlock) k_build_quads(const TI *__restrict__ img, int nx, int ny, int nz, QT *quad)
+{
+    const long long cells = (long long)(nx + 1) * (ny + 1) * (nz + 2);
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < cells;
          idx += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(idx % nx), y = (int)((idx / nx) % ny);
-        const long long dx = x + 1 < nx ? 1 : 0, dy = y + 1 < ny ? nx : 0;
-        quad[idx] = make_uint2((unsigned)img[idx] | ((unsigned)img[idx + dx] << 16),
-                               (unsigned)img[idx + dy] | ((unsigned)img[idx + dx + dy] << 16));
+        const int x = (int)(idx % (nx + 1)) - 1, y = (int)((idx / (nx + 1)) % (ny + 1)) - 1;
+        const int z = (int)(idx / ((long long)(nx + 1) * (ny + 1))) - 1;
+        const int x0 = min(max(x, 0), nx - 1), x1 = min(x + 1, nx - 1);
+        const int y0 = min(max(y, 0), ny - 1), y1 = min(y + 1, ny - 1);
+        const int zo = min(max(z, 0), nz - 1) * ny;
+        quad[idx] = quad_of<TI, QT>(img, (zo + y0) * nx + x0, (zo + y0) * nx + x1, (zo + y1) * nx + x0,
+                                    (zo + y1) * nx + x1);
     }
 }
 
@@ -749,13 +751,13 @@ cudaError_t launch_entry_work(const DevProblem *dp, const WorkEntry *entries, Ra
 
 cudaError_t launch_build_quads(const DevProblem &hp, int side, void *quad, cudaStream_t st)
 {
-    const long long N = (long long)hp.nx * hp.ny * hp.nz;
+    const long long cells = quad_cells(hp.nx, hp.ny, hp.nz);
     if (hp.dtype == MOREA_F16)
-        k_build_quads<unsigned short, uint2><<<grid_for(N), kBlock, 0, st>>>(
+        k_build_quads<unsigned short, uint2><<<grid_for(cells), kBlock, 0, st>>>(
             (const unsigned short *)hp.img[side], hp.nx, hp.ny, hp.nz, (uint2 *)quad);
     else
-        k_build_quads<float, float4><<<grid_for(N), kBlock, 0, st>>>((const float *)hp.img[side], hp.nx, hp.ny,
-                                                                     hp.nz, (float4 *)quad);
+        k_build_quads<float, float4><<<grid_for(cells), kBlock, 0, st>>>((const float *)hp.img[side], hp.nx, hp.ny,
+                                                                       hp.nz, (float4 *)quad);
     return cudaGetLastError();
 }
 

@@ -323,7 +323,7 @@ morea_status morea_create_problem(const morea_problem_desc *d, void *stream, mor
         TRY(dalloc(p, &gp_d[s], gp[s].size()));
         TRY(dalloc(p, &cs_d[s], cell_start[s].size()));
         TRY(dalloc(p, &cp_d[s], cell_pts[s].size()));
-        TRY(dalloc(p, &quad[s], (size_t)N * esz * 4));
+        TRY(dalloc(p, &quad[s], (size_t)quad_cells(nx, ny, nz) * esz * 4));
         if (continuous) {
             TRY(dalloc(p, &band[s], (size_t)N));
             if (banded) TRY(dalloc(p, &bandrow[s], (size_t)ny * nz));
@@ -357,8 +357,8 @@ morea_status morea_create_problem(const morea_problem_desc *d, void *stream, mor
     hp.dmap[1] = dmap[1];
     hp.band[0] = band[0];
     hp.band[1] = band[1];
-    hp.quad[0] = quad[0];
-    hp.quad[1] = quad[1];
+    hp.quad[0] = quad[0] + quad_origin(nx, ny) * esz * 4;
+    hp.quad[1] = quad[1] + quad_origin(nx, ny) * esz * 4;
     hp.bandrow[0] = bandrow[0];
     hp.bandrow[1] = bandrow[1];
     hp.bandd[0] = bandd[0];

@@ -109,9 +109,10 @@ __device__ __forceinline__ void make_setup(const int4 *own, const int4 *oth, con
     su.khi = min(P.nz - 1, floor_shift(mxz - H, kb));
     su.qlo[0] = mnx; su.qlo[1] = mny; su.qlo[2] = mnz;
     su.qhi[0] = mxx; su.qhi[1] = mxy; su.qhi[2] = mxz;
-    // the other copy's bounding box strictly inside [0, n-1] (margin 1/64
+    // the other copy's bounding box strictly inside (-1, n) (margin 1/64
     // voxel, far above the FP32 error of a mapped position): then the
-    // trilinear sample needs no clamping
+    // trilinear sample from the padded quad copy needs no clamping (every
+    // snapped point lies in [-0.5, n - 0.5], so this holds for every copy)
     bool inner = true;
     {
         const int om[3] = {min(min(oth[0].x, oth[1].x), min(oth[2].x, oth[3].x)),
@@ -123,7 +124,7 @@ __device__ __forceinline__ void make_setup(const int4 *own, const int4 *oth, con
         const int n[3] = {P.nx, P.ny, P.nz};
         const int margin = max(1, P.S >> 6);
         for (int a = 0; a < 3; ++a)
-            inner = inner && om[a] - H >= margin && oM[a] - H <= (n[a] - 1) * P.S - margin;
+            inner = inner && om[a] - H >= margin - P.S && oM[a] - H <= n[a] * P.S - margin;
     }
     su.valid = (D > 0.0 ? 1 : 0) | (inner ? 2 : 0);
     const long long S = P.S;

@@ -49,7 +49,7 @@ struct DevProblem {
     int n_guid, cshift;
     float wgt[kMaxGroups];           // |C^k| / |G| per guidance group
     const void *img[2];              // [0] source image I_s, [1] target image I_t
-    const void *quad[2];             // per voxel (x,y),(x+1,y),(x,y+1),(x+1,y+1) of the same z-plane
+    const void *quad[2];             // padded quad copies (quad_cells), at the element of cell (0, 0, 0)
     const float *dmap[2];            // [G][N] distance maps of the source / target contours
     const uint8_t *band[2];          // [N] bit g set where dmap[side][g] < r
     const short2 *bandrow[2];        // [nz*ny] x-range of band voxels in each image row (empty: x > y)
@@ -164,6 +164,14 @@ cudaError_t launch_full_entries(const DevProblem *dp, const DevProblem &hp, int 
 // image pass takes the items in that order.
 cudaError_t launch_entry_work(const DevProblem *dp, const WorkEntry *entries, RasterSetup *setup, TetOut *tout,
                               const int *n_entries_dev, int n_entries_host, int *rqueue, cudaStream_t st);
+// Quad copy of an image: per cell (x, y, z), -1 <= x < nx, -1 <= y < ny,
+// -1 <= z <= nz, the values at (x, y), (x+1, y), (x, y+1), (x+1, y+1) of
+// z-plane z, each index clamped into the image (so the padding repeats the
+// edge values).  Element (x, y, z) sits at (z (ny+1) + y) (nx+1) + x from the
+// element of cell (0, 0, 0), which lies quad_origin elements into the array.
+inline long long quad_cells(int nx, int ny, int nz) { return (long long)(nx + 1) * (ny + 1) * (nz + 2); }
+inline long long quad_origin(int nx, int ny) { return (long long)(nx + 1) * (ny + 2) + 1; }
+// builds the quad copy of one side into `quad` (quad_cells elements)
 cudaError_t launch_build_quads(const DevProblem &hp, int side, void *quad, cudaStream_t st);
 cudaError_t launch_band_rows(const DevProblem &hp, int side, short2 *bandrow, cudaStream_t st);
 // fills the distance word of the band records of one side (x and bits set by the host)
