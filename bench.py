@@ -96,12 +96,14 @@ def workload(seed_offset=0, name="c1", estimator="voxels"):
 # image pass (k_raster + k_guidance) per launch, averaged over one step's 21
 # launches, from an ncu capture of `bench.py --workload <w> --steps 1` (see
 # profiles/).  Valid only while the image kernels and the work-list builder
-# are unchanged: the digest covers both source files, and after any change
+# are unchanged: the digest covers their source files, and after any change
 # the bench reports null until the traffic is re-measured.
-TRAFFIC_SOURCES = ("k_raster.cu", "k_tet.cu")
+TRAFFIC_SOURCES = ("k_raster.cu", "k_tet.cu", "image_ops.cuh", "morea_device.cuh", "morea_internal.cuh")
 MEASURED_TRAFFIC = {
-    "c1": {"bytes_per_launch": 120586453,
-           "sources_sha256": "bfc75e1544307069b94793a302c877bf457e443a3495a7c7def3bd5c41ae77ab"},
+    "c2": {"bytes_per_launch": 770945073,
+           "sources_sha256": "ea32712f8b331b7651deef07d4a2ecfd50ec1f76eee85cf885102682ea69d68f"},
+    "c1": {"bytes_per_launch": 126232625,
+           "sources_sha256": "ea32712f8b331b7651deef07d4a2ecfd50ec1f76eee85cf885102682ea69d68f"},
 }
 
 
