@@ -97,7 +97,8 @@ struct __align__(16) RasterSetup {
     float s0[3];                     // vertex 0 of the own copy
     float t0[3];                     // vertex 0 of the other copy
     int valid;                         // bit 0: orientation > 0; bit 1: the other copy lies
-                                       // strictly inside [0, n-1] (no sample clamping needed)
+                                       // strictly inside (-1, n) per axis (the padded quad copy
+                                       // needs no sample clamping)
     int ilo, ihi, jlo, jhi, klo, khi;  // voxel-centre index range of the bounding box
     int qlo[3], qhi[3];                // snapped bounding box
 };
