@@ -73,3 +73,51 @@ def test_c2_partial_sampled(c2):
         r = orc.eval_partial(p.sol_src[k], p.sol_tgt[k], ns, nt, ids, base)
         assert int(folded[k]) == r["folded"]
         np.testing.assert_allclose(obj[k], r["obj"], rtol=1e-5, atol=0)
+
+
+def test_c2_rounds_in_bench_launch_shape(c2):
+    """Three partial rounds with commits in the launch shape the benchmark's
+    autotuner picks (8 blocks/SM, work-queue chunk 1; large tet copies first):
+    sampled requests against the oracle, and the committed per-tet records
+    equal a fresh full evaluation's bit for bit."""
+    p, gp, orc = c2
+    gp.set_launch(8, 1)
+    n = p.n_solutions
+    cur_s, cur_t = p.sol_src.copy(), p.sol_tgt.copy()
+    gp.eval_full(torch.as_tensor(cur_s).cuda(), torch.as_tensor(cur_t).cuda())
+    adj = synth.vertex_adjacency(p.tets, p.n_points)
+    rounds = synth.partial_requests(p, adj, 3, 4, 32, 1.0, 9)
+    rng = np.random.default_rng(10)
+    watch = (5, 130)
+    base = {k: orc.eval(cur_s[k], cur_t[k]) for k in watch}
+    for rd in rounds:
+        off = rd["chg_off"]
+        for k in range(n):
+            ids = rd["chg_pts"][off[k]:off[k + 1]]
+            rd["chg_src"][off[k]:off[k + 1]] += cur_s[k, ids] - p.sol_src[k, ids]
+            rd["chg_tgt"][off[k]:off[k + 1]] += cur_t[k, ids] - p.sol_tgt[k, ids]
+        dv = {kk: torch.as_tensor(v).cuda() for kk, v in rd.items()}
+        accept = (rng.random(n) < 0.5).astype(np.uint8)
+        accept[list(watch)] = 1
+        obj, folded, _ = gp.eval_partial(dv["slot"], dv["chg_off"], dv["chg_pts"], dv["chg_src"],
+                                         dv["chg_tgt"])
+        gp.commit_partial(torch.as_tensor(accept).cuda())
+        obj = obj.cpu().numpy()
+        assert gp.device_status() == 0
+        for k in range(n):
+            ids = rd["chg_pts"][off[k]:off[k + 1]]
+            ns, nt = cur_s[k].copy(), cur_t[k].copy()
+            ns[ids] = rd["chg_src"][off[k]:off[k + 1]]
+            nt[ids] = rd["chg_tgt"][off[k]:off[k + 1]]
+            if k in watch:
+                r = orc.eval_partial(cur_s[k], cur_t[k], ns, nt, ids, base[k])
+                assert int(folded[k]) == r["folded"]
+                np.testing.assert_allclose(obj[k], r["obj"], rtol=1e-5, atol=0)
+                base[k] = r
+            if accept[k]:
+                cur_s[k], cur_t[k] = ns, nt
+    committed = gp.read_records(n)
+    gp.eval_full(torch.as_tensor(cur_s).cuda(), torch.as_tensor(cur_t).cuda())
+    fresh = gp.read_records(n)
+    for f in ("e_img", "e_guid", "n_vox", "n_gp", "e_mag", "folded", "sev"):
+        np.testing.assert_array_equal(committed[f], fresh[f], err_msg=f)
