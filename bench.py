@@ -101,9 +101,9 @@ def workload(seed_offset=0, name="c1", estimator="voxels"):
 TRAFFIC_SOURCES = ("k_raster.cu", "k_tet.cu", "image_ops.cuh", "morea_device.cuh", "morea_internal.cuh")
 MEASURED_TRAFFIC = {
     "c2": {"bytes_per_launch": 770945073,
-           "sources_sha256": "ea32712f8b331b7651deef07d4a2ecfd50ec1f76eee85cf885102682ea69d68f"},
+           "sources_sha256": "596c46c73e5bb27788323216348159d90ef7c36985a8024580e4811243e4c898"},
     "c1": {"bytes_per_launch": 126232625,
-           "sources_sha256": "ea32712f8b331b7651deef07d4a2ecfd50ec1f76eee85cf885102682ea69d68f"},
+           "sources_sha256": "596c46c73e5bb27788323216348159d90ef7c36985a8024580e4811243e4c898"},
 }
 
 
