@@ -201,6 +201,41 @@ __global__ void __launch_bounds__(kBlock, 6) k_raster(const DevProblem *__restri
                 __syncwarp();
                 return __popc(done);
             };
+            // The 64 voxels [wbase, wbase + 64), two per lane: wbase + lane,
+            // then wbase + 32 + lane, the order of two 32-voxel windows, so the
+            // lane sums are the same.  Both halves' loads can be in flight at
+            // once.  It needs the 32 rows after head to hold every row that
+            // starts in the span (the 32nd of them starts at or after
+            // wbase + 64, or there is none); otherwise it returns -1 and does
+            // nothing.  The rows starting in the first half set bit
+            // (start - wbase) of `lo`, those in the second half bit
+            // (start - wbase - 32) of `hi`.
+            auto window2 = [&](int wbase) -> int {
+                const int r = head + 1 + lane;
+                int st = 0x7fffffff;
+                if (r < tail) st = Q.start[r & (kRowQ - 1)];
+                if (__shfl_sync(FULL, st, 31) < wbase + 2 * kWin) return -1;
+                const int rel = st - wbase;
+                const unsigned lo = __reduce_or_sync(FULL, rel < kWin ? 1u << rel : 0u);
+                const unsigned hi = __reduce_or_sync(FULL, rel >= kWin && rel < 2 * kWin ? 1u << (rel - kWin) : 0u);
+                const unsigned done = __ballot_sync(FULL, st <= wbase + 2 * kWin);
+                const int q0 = (head + __popc(lo & upto)) & (kRowQ - 1);
+                const int q1 = (head + __popc(lo) + __popc(hi & upto)) & (kRowQ - 1);
+                {
+                    const int2 db = Q.db[q0];
+                    const float4 rq = Q.r[q0];
+                    const float4 mc = Q.mcol;
+                    voxel(wbase + lane, db.x, db.y, rq.x, rq.y, rq.z, mc.x, mc.y, mc.z, mc.w);
+                }
+                {
+                    const int2 db = Q.db[q1];
+                    const float4 rq = Q.r[q1];
+                    const float4 mc = Q.mcol;
+                    voxel(wbase + kWin + lane, db.x, db.y, rq.x, rq.y, rq.z, mc.x, mc.y, mc.z, mc.w);
+                }
+                __syncwarp();
+                return __popc(done);
+            };
             // Rows of the bounding box that can meet the copy, 32 z-slices at
             // a time: lane l finds the y-extent [jl, jl + ns) of slice
             // klo + kc + l, a warp scan numbers the rows of the chunk, and the
@@ -283,6 +318,14 @@ __global__ void __launch_bounds__(kBlock, 6) k_raster(const DevProblem *__restri
                     total += batch_total;
                     __syncwarp();
                     while (total - pend >= kWin) {
+                        if (total - pend >= 2 * kWin) {
+                            const int adv = window2(pend);
+                            if (adv >= 0) {
+                                head += adv;
+                                pend += 2 * kWin;
+                                continue;
+                            }
+                        }
                         head += window(pend, kWin);
                         pend += kWin;
                     }
