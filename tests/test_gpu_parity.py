@@ -325,3 +325,27 @@ def test_c1_full_size_sampled(mo):
         nt[ids] = rd["chg_tgt"][off[k]:off[k + 1]]
         r = orc.eval_partial(p.sol_src[k], p.sol_tgt[k], ns, nt, ids, res[k])
         assert_obj_close(pobj[k], r["obj"], f"c1 request {k}")
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float16])
+def test_short_and_long_rows(mo, dtype):
+    """One mesh with cells of 1.5 voxels (rows of one or two voxel centres,
+    more than 32 row starts in 64 voxels, so the image pass falls back to
+    32-voxel windows) beside cells of 24 voxels (long rows, taken 64 voxels
+    per window two voxels a lane).  Per-tet sums against the oracle."""
+    img_s = random_image((40, 40, 40), 21, dtype=dtype)
+    img_t = random_image((40, 40, 40), 22, dtype=dtype)
+    axis = np.concatenate([np.arange(-0.5, 15.0, 1.5), [15.5, 39.5]])
+    pts, tets = box_lattice(axis, axis, axis)
+    rng = np.random.default_rng(23)
+    interior = np.all((pts > 0.0) & (pts < 39.0), axis=1)
+    n = 2
+    src = np.repeat(pts[None], n, axis=0).astype(np.float32)
+    tgt = src.copy()
+    tgt[:, interior] += rng.uniform(-0.2, 0.2, size=(n, int(interior.sum()), 3)).astype(np.float32)
+    prob = problem(img_s, img_t, pts, tets, g_mode=2, sol_src=src, sol_tgt=tgt)
+    gp, orc, _ = check_against_oracle(mo, prob)
+    recs = gp.read_records(n)
+    vox = recs["n_vox"].sum(axis=2)
+    assert vox.min() <= 2 and vox.max() > 2000        # both kinds of tets are present
+    assert gp.device_status() == 0
